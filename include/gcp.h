@@ -1,0 +1,171 @@
+/*
+ * gcp.h -- C ABI of libgcp: generalized canonical purification (GCP, the
+ * paper's hole-particle canonical purification, HPCP) on one GB300 GPU.
+ *
+ * Problem (paper's problem statement, Eq. mcw4a with the footnote on
+ * orthonormal bases): given a real symmetric Hamiltonian H (M x M, in an
+ * orthonormal basis) and an electron count 0 <= N <= M, return the
+ * idempotent density matrix D (D^2 = D) with Tr D = N that minimises
+ * E = Tr(H D), without diagonalising H.
+ *
+ * Method:
+ *   guess   D_0 = beta_1 I + beta_2 (mu I - H)                 (Eq. dmguess)
+ *           beta_1 = theta = N/M, mu = Tr H / M,
+ *           beta_2 = min{theta/(H_max - mu), (1-theta)/(mu - H_min)},
+ *           H_min/H_max Gershgorin bounds                      (Eq. pmcpguess)
+ *   step    c_n = Tr(D^2 - D^3) / Tr(D - D^2)                   (Eq. mcwgamb)
+ *           D_{n+1} = D + 2 (D^2 (I-D) - c_n D (I-D))           (Eq. hpcp3)
+ *                   = (1-2c) D + (2+2c) D^2 - 2 D^3
+ *   stop    ||D^2 - D||_F <= tol, or Tr(D (I-D)) <= tol (the paper's test,
+ *           text after Eq. hpcp3)
+ *   energy  E = Tr(H D)
+ *
+ * Conventions for every entry point:
+ *   - Matrix arguments are DEVICE pointers owned by the caller, row-major
+ *     with leading dimension `ld` (elements, ld >= M).  Because every matrix
+ *     here is symmetric, row- and column-major are the same; H is read in
+ *     full and must be symmetric (it is not checked).
+ *   - `dtype` arguments take gcp_dtype: GCP_F64 (double) or GCP_F32 (float).
+ *   - Small outputs (gcp_result, the info arrays) are HOST pointers, written
+ *     after the call has synchronised its stream.  Every call here is
+ *     synchronous at exit with respect to `opt->stream`.
+ *   - The handle owns all workspace (device memory, graphs, tensor maps);
+ *     workspace grows on demand and is released by gcp_destroy.  A handle
+ *     must not be used from two host threads at once.
+ *   - Errors are returned as gcp_status and never abort the process.
+ *     GCP_ERR_NOT_CONVERGED still fills D_out and the result.
+ *     gcp_last_error() gives a one-line description of the last failure.
+ */
+#ifndef GCP_H_
+#define GCP_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GCP_OK = 0,
+  GCP_ERR_INVALID_ARG = 1,     /* bad pointer, size, dtype or option */
+  GCP_ERR_NOT_CONVERGED = 2,   /* max_iter reached or stagnated above tol */
+  GCP_ERR_ILL_CONDITIONED = 3, /* c_0 outside [0,1]: Eqs. pmcpcons2-3 violated */
+  GCP_ERR_NO_GAP = 4,          /* H = mu I: zero-width Gershgorin interval */
+  GCP_ERR_NONFINITE = 5,       /* NaN/Inf in a trace */
+  GCP_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+  GCP_ERR_CUDA = 7,            /* a CUDA runtime/driver call failed */
+  GCP_ERR_UNSUPPORTED = 8,     /* combination not built */
+  GCP_ERR_NO_CHECKPOINT = 9    /* gcp_backward without a matching forward */
+} gcp_status;
+
+typedef enum { GCP_F64 = 0, GCP_F32 = 1 } gcp_dtype;
+
+/* Arithmetic of the matrix products.
+ *   GCP_FP64        FP64 products (SIMT DFMA) and FP64 state throughout.
+ *   GCP_FP16X3      split-FP16 tensor-core products (tcgen05, FP32
+ *                   accumulation in TMEM, 3 products per GEMM) on the
+ *                   shifted state X = D - theta I held in FP32; stops at
+ *                   its own accuracy floor.
+ *   GCP_BF16X3      as FP16X3 with BF16 halves.
+ *   GCP_MIXED_FP16  FP16X3 until the residual stagnates, then FP64 steps
+ *                   until the stop test holds.
+ *   GCP_MIXED_BF16  BF16X3 bulk, FP64 refinement.                       */
+typedef enum {
+  GCP_FP64 = 0,
+  GCP_FP16X3 = 1,
+  GCP_BF16X3 = 2,
+  GCP_MIXED_FP16 = 3,
+  GCP_MIXED_BF16 = 4
+} gcp_precision;
+
+typedef enum {
+  GCP_STOP_IDEMP_FRO = 0,  /* ||D^2 - D||_F <= tol (computed elementwise) */
+  GCP_STOP_TRACE_DDBAR = 1 /* Tr(D - D^2) <= tol (the paper's test) */
+} gcp_stop;
+
+typedef struct {
+  int prec;            /* gcp_precision (default GCP_FP64) */
+  int stop;            /* gcp_stop (default GCP_STOP_IDEMP_FRO) */
+  double tol;          /* stop tolerance (default 1e-12) */
+  int max_iter;        /* cap on steps (default 100) */
+  int fixed_iters;     /* > 0: run exactly this many steps, no stop test;
+                          steps past the 0/0 guard become identity steps */
+  int ckpt_every;      /* checkpoint interval for gcp_backward (default 8) */
+  int history_cap;     /* > 0: record up to this many per-step records */
+  int use_graph;       /* 1 (default): device-side loop in one CUDA graph;
+                          0: host-driven loop (debugging) */
+  void* stream;        /* cudaStream_t; NULL = legacy default stream */
+} gcp_options;
+
+typedef struct {
+  int status;        /* gcp_status of the solve */
+  int iters;         /* steps applied (all phases) */
+  int iters_lowp;    /* steps applied in the split-precision phase */
+  int iters_fp64;    /* steps applied in FP64 */
+  double trace;      /* Tr D of the returned D (FP64 sum) */
+  double energy;     /* E = Tr(H D) of the returned D */
+  double idem_fro;   /* ||D^2 - D||_F at the last evaluated iterate */
+  double trace_ddbar;/* Tr(D - D^2) at the last evaluated iterate */
+  double c_last;     /* last c_n used */
+  double mu, beta2, hmin, hmax; /* guess parameters (Eq. pmcpguess) */
+} gcp_result;
+
+/* Per-step record written when history_cap > 0 (gcp_get_history):
+ * {n, T1 = Tr D, T2 = Tr D^2, T3 = Tr D^3, R = ||D^2-D||_F, c_n, E_n, phase}
+ * phase: 0 = FP64, 1 = split precision.  c_n is NaN on the final record. */
+#define GCP_HISTORY_FIELDS 8
+
+void gcp_default_options(gcp_options* opt);
+const char* gcp_status_string(int status);
+
+gcp_status gcp_create(void** handle);
+gcp_status gcp_destroy(void* handle);
+const char* gcp_last_error(void* handle);
+
+/* Canonical initial guess (Eq. dmguess, Eq. pmcpguess).
+ * H: device, M x M, ld, h_dtype.  D0: device, M x M, ldd, d_dtype (written).
+ * info (host, 5 doubles, may be NULL): mu, beta2, H_min, H_max, theta.
+ * Returns GCP_ERR_NO_GAP (D0 = theta I) when the Gershgorin interval has
+ * zero width.  0 < N < M required (the trivial fillings have no guess). */
+gcp_status gcp_init_guess(void* handle, const void* H, int M, int N, int ld, int h_dtype,
+                          void* D0, int ldd, int d_dtype, double* info,
+                          const gcp_options* opt);
+
+/* One step of Eq. hpcp3 in place on D (device, M x M, ld, d_dtype), in the
+ * arithmetic opt->prec selects (GCP_FP64 requires d_dtype GCP_F64; the
+ * split-precision modes take GCP_F32 and theta = N/M for the shift).
+ * out (host, 6 doubles, may be NULL): T1, T2, T3, R = ||D^2 - D||_F, c, and
+ * 1.0 if the update was applied (0.0 when Tr(D - D^2) was at the 0/0 guard). */
+gcp_status gcp_step(void* handle, void* D, int M, int N, int ld, int d_dtype, double* out,
+                    const gcp_options* opt);
+
+/* Full solve: guess, recursion with device-side stop test, energy.
+ * H: device, M x M, ld, h_dtype.  D_out: device, M x M, ldd, d_dtype.
+ * res: host (may be NULL).  N = 0 and N = M return D = 0 / D = I. */
+gcp_status gcp_solve(void* handle, const void* H, int M, int N, int ld, int h_dtype,
+                     void* D_out, int ldd, int d_dtype, gcp_result* res,
+                     const gcp_options* opt);
+
+/* Copy the history of the last gcp_solve (host buffer, cap records of
+ * GCP_HISTORY_FIELDS doubles); *n_out = records written. */
+gcp_status gcp_get_history(void* handle, double* out, int cap, int* n_out);
+
+/* Many independent solves of uneven size in one call.  H[b], D_out[b]:
+ * device pointers; M[b], N[b], ld[b]: host arrays of length batch; all H in
+ * h_dtype and all D in d_dtype.  res: host array of `batch` results (may be
+ * NULL).  Instances converge independently (per-instance c_n and stop). */
+gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, const int* M,
+                             const int* N, const int* ld, int h_dtype, void* const* D_out,
+                             int d_dtype, gcp_result* res, const gcp_options* opt);
+
+/* Reverse-mode derivative of L = <G_D, D_K> + g_E * Tr(H D_K), where D_K is
+ * the iterate after exactly opt->fixed_iters steps from the guess of H.
+ * H: device M x M (ld, h_dtype); G_D: device M x M (ld, h_dtype) or NULL;
+ * dL_dH: device M x M (ld, h_dtype), written, symmetric.  Re-runs the
+ * forward pass itself, storing a checkpoint every opt->ckpt_every steps and
+ * recomputing the iterates in between. */
+gcp_status gcp_backward(void* handle, const void* H, int M, int N, int ld, int h_dtype,
+                        const void* G_D, double g_E, void* dL_dH, const gcp_options* opt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCP_H_ */

@@ -1,0 +1,670 @@
+// libgcp C ABI: handle, workspace, graph-captured solve loop and the
+// entry points declared in include/gcp.h.
+//
+// A solve is recorded once into a CUDA graph and replayed while its
+// arguments (pointers, sizes, options) stay the same:
+//   guess (3 kernels) -> [WHILE split phase: 2 x (GEMM1, control, GEMM2)]
+//   -> [transition to FP64] -> [WHILE FP64 phase: 2 x (GEMM1, control, GEMM2)]
+//   -> copy-out -> energy.
+// The WHILE conditions are set on the device by the control kernel, so the
+// host waits only once, for the final scalars.  Each body holds two steps
+// because the ping-pong buffers are baked into the captured kernels; a step
+// after the stop test fired exits at once.
+#include <cuda.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "gcp_internal.cuh"
+
+using namespace gcp;
+
+namespace {
+
+constexpr float kSplitScale = 1024.0f;
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+
+struct Handle {
+  std::string err;
+  cudaStream_t cap = nullptr;   // capture stream (solve graphs)
+  cudaStream_t body = nullptr;  // capture stream for WHILE bodies
+  // FP64 state
+  int m64 = 0;
+  double* D64[2] = {nullptr, nullptr};
+  double* S64 = nullptr;
+  // split state (Mp x Mp)
+  int mp = 0;
+  int tc_bf16 = -1;
+  float* X[2] = {nullptr, nullptr};
+  void* Xh[2] = {nullptr, nullptr};
+  void* Xl[2] = {nullptr, nullptr};
+  float* Sig = nullptr;
+  void* Sh = nullptr;
+  void* Sl = nullptr;
+  TcOperands* opX[2] = {nullptr, nullptr};
+  TcOperands* opS = nullptr;
+  // scalars and partials
+  double* part = nullptr;
+  size_t part_n = 0;
+  double* gpart = nullptr;
+  size_t gpart_n = 0;
+  State* st = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int hist_last = 0;
+  // cached solve graph
+  std::vector<char> key;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+gcp_status fail(Handle* h, gcp_status s, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, GCP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+template <typename T>
+cudaError_t grow(T** p, size_t n_old, size_t n_new) {
+  if (n_new <= n_old && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  return cudaMalloc((void**)p, n_new * sizeof(T));
+}
+
+void drop_graph(Handle* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  h->key.clear();
+}
+
+gcp_status ensure_common(Handle* h, size_t ntiles, int M, int hist_cap) {
+  if (!h->st) {
+    CK(cudaMalloc((void**)&h->st, sizeof(State)));
+    CK(cudaMemset(h->st, 0, sizeof(State)));
+  }
+  if (ntiles * kPartFields > h->part_n) {
+    drop_graph(h);
+    CK(grow(&h->part, h->part_n, ntiles * kPartFields));
+    h->part_n = ntiles * kPartFields;
+  }
+  const size_t gp = (size_t)guess_partial_blocks(M) * 4;
+  if (gp > h->gpart_n) {
+    drop_graph(h);
+    CK(grow(&h->gpart, h->gpart_n, gp));
+    h->gpart_n = gp;
+  }
+  if (hist_cap > h->hist_cap) {
+    drop_graph(h);
+    CK(grow(&h->hist, (size_t)h->hist_cap * GCP_HISTORY_FIELDS,
+            (size_t)hist_cap * GCP_HISTORY_FIELDS));
+    h->hist_cap = hist_cap;
+  }
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  if (!h->body) CK(cudaStreamCreateWithFlags(&h->body, cudaStreamNonBlocking));
+  return GCP_OK;
+}
+
+gcp_status ensure_f64(Handle* h, int M) {
+  if (M <= h->m64) return GCP_OK;
+  drop_graph(h);
+  const size_t n = (size_t)M * M;
+  for (int i = 0; i < 2; ++i) {
+    if (h->D64[i]) cudaFree(h->D64[i]);
+    h->D64[i] = nullptr;
+    CK(cudaMalloc((void**)&h->D64[i], n * sizeof(double)));
+  }
+  if (h->S64) cudaFree(h->S64);
+  h->S64 = nullptr;
+  CK(cudaMalloc((void**)&h->S64, n * sizeof(double)));
+  h->m64 = M;
+  return GCP_OK;
+}
+
+gcp_status ensure_split(Handle* h, int Mp, int bf16) {
+  if (Mp == h->mp && bf16 == h->tc_bf16) return GCP_OK;
+  drop_graph(h);
+  for (int i = 0; i < 2; ++i) {
+    if (h->opX[i]) tc_free_operands(h->opX[i]);
+    h->opX[i] = nullptr;
+  }
+  if (h->opS) tc_free_operands(h->opS);
+  h->opS = nullptr;
+  if (Mp != h->mp) {
+    const size_t n = (size_t)Mp * Mp;
+    auto fr = [](void* p) {
+      if (p) cudaFree(p);
+    };
+    for (int i = 0; i < 2; ++i) {
+      fr(h->X[i]);
+      fr(h->Xh[i]);
+      fr(h->Xl[i]);
+      h->X[i] = nullptr;
+      h->Xh[i] = h->Xl[i] = nullptr;
+      CK(cudaMalloc((void**)&h->X[i], n * 4));
+      CK(cudaMalloc(&h->Xh[i], n * 2));
+      CK(cudaMalloc(&h->Xl[i], n * 2));
+    }
+    fr(h->Sig);
+    fr(h->Sh);
+    fr(h->Sl);
+    h->Sig = nullptr;
+    h->Sh = h->Sl = nullptr;
+    CK(cudaMalloc((void**)&h->Sig, n * 4));
+    CK(cudaMalloc(&h->Sh, n * 2));
+    CK(cudaMalloc(&h->Sl, n * 2));
+    h->mp = Mp;
+  }
+  char err[256] = {0};
+  for (int i = 0; i < 2; ++i)
+    if (tc_make_operands(&h->opX[i], h->Xh[i], h->Xl[i], Mp, bf16, err, sizeof err))
+      return fail(h, GCP_ERR_CUDA, "%s", err);
+  if (tc_make_operands(&h->opS, h->Sh, h->Sl, Mp, bf16, err, sizeof err))
+    return fail(h, GCP_ERR_CUDA, "%s", err);
+  h->tc_bf16 = bf16;
+  return GCP_OK;
+}
+
+bool is_split(int prec) { return prec >= GCP_FP16X3 && prec <= GCP_MIXED_BF16; }
+bool is_mixed(int prec) { return prec == GCP_MIXED_FP16 || prec == GCP_MIXED_BF16; }
+int split_bf16(int prec) { return prec == GCP_BF16X3 || prec == GCP_MIXED_BF16; }
+
+struct SolveArgs {
+  const void* H;
+  int M, N, ld, h_f64;
+  void* D_out;
+  int ldd, d_f64;
+  gcp_options o;
+};
+
+Ctl make_ctl(const SolveArgs& a, int phase, int final_phase) {
+  Ctl c{};
+  c.M = a.M;
+  c.N = a.N;
+  c.stop = a.o.stop;
+  c.max_iter = a.o.max_iter;
+  c.fixed_iters = a.o.fixed_iters;
+  c.hist_cap = a.o.history_cap;
+  c.phase = phase;
+  c.final_phase = final_phase;
+  c.tol = a.o.tol;
+  c.u = phase == 1 ? kU32 : kU64;
+  return c;
+}
+
+// One step of the FP64 phase: GEMM1 -> control -> GEMM2 (buffers src -> dst).
+gcp_status rec_f64_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
+                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  const int M = a.M, ld = M;
+  const void* Hh = a.o.history_cap > 0 ? a.H : nullptr;
+  launch_f64_gemm1(h->D64[src], h->S64, M, ld, Hh, a.h_f64, a.ld, h->part, h->st, s);
+  launch_control(h->part, f64_num_tiles(M), h->st, a.o.history_cap > 0 ? h->hist : nullptr, ctl,
+                 (unsigned long long)cond, use_cond, s);
+  launch_f64_gemm2(h->S64, h->D64[src], h->D64[src ^ 1], M, ld, h->st, s);
+  CK(cudaPeekAtLastError());
+  return GCP_OK;
+}
+
+// One step of the split phase on the shifted state.
+gcp_status rec_split_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
+                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  const int M = a.M, Mp = h->mp, bf = h->tc_bf16;
+  const void* Hh = a.o.history_cap > 0 ? a.H : nullptr;
+  if (tc_launch_gemm1(h->opX[src], h->X[src], h->Sig, h->Sh, h->Sl, M, Mp, Hh, a.h_f64, a.ld,
+                      h->part, h->st, bf, kSplitScale, nullptr, s))
+    return fail(h, GCP_ERR_CUDA, "tcgen05 GEMM1 launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  launch_control(h->part, tc_num_tiles(Mp), h->st, a.o.history_cap > 0 ? h->hist : nullptr, ctl,
+                 (unsigned long long)cond, use_cond, s);
+  if (tc_launch_gemm2(h->opS, h->opX[src], h->X[src], h->Sig, h->X[src ^ 1], h->Xh[src ^ 1],
+                      h->Xl[src ^ 1], M, Mp, h->st, bf, kSplitScale, nullptr, s))
+    return fail(h, GCP_ERR_CUDA, "tcgen05 GEMM2 launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  CK(cudaPeekAtLastError());
+  return GCP_OK;
+}
+
+// Add a WHILE node at the current capture position of `s` and capture its
+// body (two steps) on h->body.
+template <typename StepFn>
+gcp_status rec_while(Handle* h, cudaStream_t s, StepFn step) {
+  cudaStreamCaptureStatus cst;
+  unsigned long long id = 0;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cst, &id, &g, &deps, &edata, &nd));
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = cond;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, edata, nd, &p));
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(h->body, bodyg, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  gcp_status r = step(0, cond, h->body);
+  if (r == GCP_OK) r = step(1, cond, h->body);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->body, &out);
+  if (r != GCP_OK) return r;
+  if (e != cudaSuccess) return fail(h, GCP_ERR_CUDA, "body capture: %s", cudaGetErrorString(e));
+  return GCP_OK;
+}
+
+// Record the whole solve on stream s (captured, or eager with a host loop).
+gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool graph) {
+  const int M = a.M, N = a.N;
+  const bool split = is_split(a.o.prec), mixed = is_mixed(a.o.prec);
+  launch_guess_reduce(a.H, a.h_f64, M, a.ld, h->gpart, s);
+  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, h->st, s);
+  launch_state_init(h->st, split ? 1 : 0, s);
+  if (split) {
+    launch_guess_write_x(a.H, a.h_f64, M, a.ld, h->X[0], h->Xh[0], h->Xl[0], h->mp, h->tc_bf16,
+                         kSplitScale, h->st, s);
+  } else {
+    launch_guess_write_d(a.H, a.h_f64, M, a.ld, h->D64[0], 1, M, M, h->st, s);
+  }
+  CK(cudaPeekAtLastError());
+  if (split) {
+    const Ctl ctl = make_ctl(a, 1, mixed ? 0 : 1);
+    auto step = [&](int src, cudaGraphConditionalHandle c, cudaStream_t ss) {
+      return rec_split_step(h, a, src, ctl, c, graph ? 1 : 0, ss);
+    };
+    if (graph) {
+      gcp_status r = rec_while(h, s, step);
+      if (r != GCP_OK) return r;
+    } else {
+      for (int it = 0;; ++it) {
+        gcp_status r = step(it & 1, 0, s);
+        if (r != GCP_OK) return r;
+        State hs;
+        CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hs.stopped) break;
+      }
+    }
+  }
+  if (mixed) {
+    launch_phase_begin(h->st, 0, s);
+    launch_x_to_d64(h->X[0], h->X[1], h->st, M, h->mp, h->D64[0], M, N, s);
+  }
+  if (!split || mixed) {
+    const Ctl ctl = make_ctl(a, 0, 1);
+    auto step = [&](int src, cudaGraphConditionalHandle c, cudaStream_t ss) {
+      return rec_f64_step(h, a, src, ctl, c, graph ? 1 : 0, ss);
+    };
+    if (graph) {
+      gcp_status r = rec_while(h, s, step);
+      if (r != GCP_OK) return r;
+    } else {
+      for (int it = 0;; ++it) {
+        gcp_status r = step(it & 1, 0, s);
+        if (r != GCP_OK) return r;
+        State hs;
+        CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hs.stopped) break;
+      }
+    }
+  }
+  if (split && !mixed)
+    launch_copy_out_x(h->X[0], h->X[1], h->st, M, h->mp, a.D_out, a.d_f64, a.ldd, s);
+  else
+    launch_copy_out_f64(h->D64[0], h->D64[1], h->st, M, M, a.D_out, a.d_f64, a.ldd, s);
+  launch_energy(a.D_out, a.d_f64, a.ldd, a.H, a.h_f64, a.ld, M, h->gpart, h->st, s);
+  CK(cudaPeekAtLastError());
+  return GCP_OK;
+}
+
+std::vector<char> make_key(const SolveArgs& a) {
+  std::vector<char> k(sizeof(SolveArgs));
+  SolveArgs c = a;
+  c.o.stream = nullptr;
+  memcpy(k.data(), &c, sizeof c);
+  return k;
+}
+
+void fill_result(const State& hs, gcp_result* res) {
+  if (!res) return;
+  res->status = hs.status;
+  res->iters = hs.n;
+  res->iters_lowp = hs.n_lowp;
+  res->iters_fp64 = hs.n - hs.n_lowp;
+  res->trace = hs.T1;
+  res->energy = hs.E;
+  res->idem_fro = hs.R;
+  res->trace_ddbar = hs.T1 - hs.T2;
+  res->c_last = hs.c;
+  res->mu = hs.mu;
+  res->beta2 = hs.beta2;
+  res->hmin = hs.hmin;
+  res->hmax = hs.hmax;
+}
+
+bool valid_dtype(int d) { return d == GCP_F64 || d == GCP_F32; }
+
+}  // namespace
+
+extern "C" {
+
+void gcp_default_options(gcp_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->prec = GCP_FP64;
+  o->stop = GCP_STOP_IDEMP_FRO;
+  o->tol = 1e-12;
+  o->max_iter = 100;
+  o->fixed_iters = 0;
+  o->ckpt_every = 8;
+  o->history_cap = 0;
+  o->use_graph = 1;
+  o->stream = nullptr;
+}
+
+const char* gcp_status_string(int s) {
+  switch (s) {
+    case GCP_OK: return "ok";
+    case GCP_ERR_INVALID_ARG: return "invalid argument";
+    case GCP_ERR_NOT_CONVERGED: return "not converged";
+    case GCP_ERR_ILL_CONDITIONED: return "ill-conditioned initial guess";
+    case GCP_ERR_NO_GAP: return "no gap (H = mu I)";
+    case GCP_ERR_NONFINITE: return "non-finite trace";
+    case GCP_ERR_TIMEOUT: return "device wait timed out";
+    case GCP_ERR_CUDA: return "CUDA error";
+    case GCP_ERR_UNSUPPORTED: return "unsupported";
+    case GCP_ERR_NO_CHECKPOINT: return "no checkpoint";
+    default: return "unknown status";
+  }
+}
+
+gcp_status gcp_create(void** out) {
+  if (!out) return GCP_ERR_INVALID_ARG;
+  *out = new Handle;
+  return GCP_OK;
+}
+
+gcp_status gcp_destroy(void* hv) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  drop_graph(h);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->D64[i]);
+    cudaFree(h->X[i]);
+    cudaFree(h->Xh[i]);
+    cudaFree(h->Xl[i]);
+    if (h->opX[i]) tc_free_operands(h->opX[i]);
+  }
+  if (h->opS) tc_free_operands(h->opS);
+  cudaFree(h->S64);
+  cudaFree(h->Sig);
+  cudaFree(h->Sh);
+  cudaFree(h->Sl);
+  cudaFree(h->part);
+  cudaFree(h->gpart);
+  cudaFree(h->st);
+  cudaFree(h->hist);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->body) cudaStreamDestroy(h->body);
+  delete h;
+  return GCP_OK;
+}
+
+const char* gcp_last_error(void* hv) {
+  Handle* h = (Handle*)hv;
+  return h ? h->err.c_str() : "null handle";
+}
+
+gcp_status gcp_init_guess(void* hv, const void* H, int M, int N, int ld, int h_dtype, void* D0,
+                          int ldd, int d_dtype, double* info, const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  if (!H || !D0 || M <= 0 || N <= 0 || N >= M || ld < M || ldd < M || !valid_dtype(h_dtype) ||
+      !valid_dtype(d_dtype))
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_init_guess: bad arguments");
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  gcp_status r = ensure_common(h, 1, M, 0);
+  if (r != GCP_OK) return r;
+  launch_guess_reduce(H, h_dtype == GCP_F64, M, ld, h->gpart, s);
+  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, h->st, s);
+  launch_guess_write_d(H, h_dtype == GCP_F64, M, ld, D0, d_dtype == GCP_F64, ldd, M, h->st, s);
+  CK(cudaPeekAtLastError());
+  State hs;
+  CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    info[0] = hs.mu;
+    info[1] = hs.beta2;
+    info[2] = hs.hmin;
+    info[3] = hs.hmax;
+    info[4] = hs.theta;
+  }
+  return hs.no_gap ? fail(h, GCP_ERR_NO_GAP, "H has a zero-width spectrum bound") : GCP_OK;
+}
+
+gcp_status gcp_step(void* hv, void* D, int M, int N, int ld, int d_dtype, double* out,
+                    const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  if (!D || M <= 0 || N < 0 || N > M || ld < M || !valid_dtype(d_dtype) || o.prec < 0 ||
+      o.prec > GCP_MIXED_BF16)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_step: bad arguments");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  SolveArgs a{};
+  a.H = nullptr;
+  a.M = M;
+  a.N = N;
+  a.ld = ld;
+  a.h_f64 = 1;
+  a.o = o;
+  a.o.fixed_iters = 1;  // one step, no stop test
+  a.o.history_cap = 0;
+  const bool split = is_split(o.prec) && !is_mixed(o.prec);
+  gcp_status r;
+  if (split) {
+    const int Mp = tc_pad(M);
+    if ((r = ensure_common(h, tc_num_tiles(Mp), M, 0)) != GCP_OK) return r;
+    if ((r = ensure_split(h, Mp, split_bf16(o.prec))) != GCP_OK) return r;
+  } else {
+    if ((r = ensure_common(h, f64_num_tiles(M), M, 0)) != GCP_OK) return r;
+    if ((r = ensure_f64(h, M)) != GCP_OK) return r;
+  }
+  // state: theta for the shift, loop fields reset
+  State init;
+  memset(&init, 0, sizeof init);
+  init.theta = (double)N / (double)M;
+  CK(cudaMemcpyAsync(h->st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+  launch_state_init(h->st, split ? 1 : 0, s);
+  if (split) {
+    launch_d_to_x(D, d_dtype == GCP_F64, M, ld, h->X[0], h->Xh[0], h->Xl[0], h->mp, h->tc_bf16,
+                  kSplitScale, init.theta, s);
+    if ((r = rec_split_step(h, a, 0, make_ctl(a, 1, 1), 0, 0, s)) != GCP_OK) return r;
+    launch_copy_out_x(h->X[0], h->X[1], h->st, M, h->mp, D, d_dtype == GCP_F64, ld, s);
+  } else {
+    launch_convert(D, d_dtype == GCP_F64, ld, h->D64[0], 1, M, M, s);
+    if ((r = rec_f64_step(h, a, 0, make_ctl(a, 0, 1), 0, 0, s)) != GCP_OK) return r;
+    launch_copy_out_f64(h->D64[0], h->D64[1], h->st, M, M, D, d_dtype == GCP_F64, ld, s);
+  }
+  CK(cudaPeekAtLastError());
+  State hs;
+  CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");
+  if (out) {
+    out[0] = hs.T1;
+    out[1] = hs.T2;
+    out[2] = hs.T3;
+    out[3] = hs.R;
+    out[4] = hs.c;
+    out[5] = hs.n > 0 && hs.apply ? 1.0 : 0.0;
+  }
+  return GCP_OK;
+}
+
+gcp_status gcp_solve(void* hv, const void* H, int M, int N, int ld, int h_dtype, void* D_out,
+                     int ldd, int d_dtype, gcp_result* res, const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  if (!H || !D_out || M <= 0 || N < 0 || N > M || ld < M || ldd < M || !valid_dtype(h_dtype) ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
+      o.history_cap < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1))
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve: bad arguments");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  if (res) memset(res, 0, sizeof *res);
+  if (N == 0 || N == M) {
+    launch_fill(nullptr, D_out, d_dtype == GCP_F64, M, ldd, N == 0 ? 0.0 : 1.0, s);
+    CK(cudaPeekAtLastError());
+    CK(cudaStreamSynchronize(s));
+    if (res) {
+      res->status = GCP_OK;
+      res->trace = N;
+      res->energy = 0.0;
+    }
+    if (N == M && res) {
+      // E = Tr H for D = I: computed by the energy kernel on the filled D
+      gcp_status r = ensure_common(h, 1, M, 0);
+      if (r != GCP_OK) return r;
+      launch_energy(D_out, d_dtype == GCP_F64, ldd, H, h_dtype == GCP_F64, ld, M, h->gpart, h->st,
+                    s);
+      State hs;
+      CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      res->energy = hs.E;
+    }
+    return GCP_OK;
+  }
+  SolveArgs a{};
+  a.H = H;
+  a.M = M;
+  a.N = N;
+  a.ld = ld;
+  a.h_f64 = h_dtype == GCP_F64;
+  a.D_out = D_out;
+  a.ldd = ldd;
+  a.d_f64 = d_dtype == GCP_F64;
+  a.o = o;
+  const bool split = is_split(o.prec), mixed = is_mixed(o.prec);
+  gcp_status r;
+  size_t nt = 1;
+  if (split) nt = tc_num_tiles(tc_pad(M));
+  if (!split || mixed) nt = nt > (size_t)f64_num_tiles(M) ? nt : (size_t)f64_num_tiles(M);
+  if ((r = ensure_common(h, nt, M, o.history_cap)) != GCP_OK) return r;
+  if (split && (r = ensure_split(h, tc_pad(M), split_bf16(o.prec))) != GCP_OK) return r;
+  if ((!split || mixed) && (r = ensure_f64(h, M)) != GCP_OK) return r;
+  if (o.use_graph) {
+    std::vector<char> key = make_key(a);
+    if (!h->exec || key != h->key) {
+      drop_graph(h);
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
+      r = record_solve(h, a, h->cap, true);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+      if (r != GCP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess)
+        return fail(h, GCP_ERR_CUDA, "solve capture: %s", cudaGetErrorString(e));
+      h->graph = g;
+      CK(cudaGraphInstantiate(&h->exec, g, 0));
+      h->key = key;
+    }
+    CK(cudaGraphLaunch(h->exec, s));
+  } else {
+    if ((r = record_solve(h, a, s, false)) != GCP_OK) return r;
+  }
+  State hs;
+  CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->hist_last = hs.hist_n;
+  fill_result(hs, res);
+  if (res) res->energy = hs.E;
+  if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");
+  if (hs.status != GCP_OK)
+    return fail(h, (gcp_status)hs.status, "solve ended: %s", gcp_status_string(hs.status));
+  return GCP_OK;
+}
+
+gcp_status gcp_get_history(void* hv, double* out, int cap, int* n_out) {
+  Handle* h = (Handle*)hv;
+  if (!h || !out || cap < 0) return GCP_ERR_INVALID_ARG;
+  int n = h->hist_last < cap ? h->hist_last : cap;
+  if (n > h->hist_cap) n = h->hist_cap;
+  if (n > 0) CK(cudaMemcpy(out, h->hist, (size_t)n * GCP_HISTORY_FIELDS * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  return GCP_OK;
+}
+
+gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const int* M, const int* N,
+                             const int* ld, int h_dtype, void* const* D_out, int d_dtype,
+                             gcp_result* res, const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  (void)batch;
+  (void)H;
+  (void)M;
+  (void)N;
+  (void)ld;
+  (void)h_dtype;
+  (void)D_out;
+  (void)d_dtype;
+  (void)res;
+  (void)opt;
+  return fail(h, GCP_ERR_UNSUPPORTED, "gcp_solve_batched: not built yet");
+}
+
+gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dtype,
+                        const void* G_D, double g_E, void* dL_dH, const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  (void)H;
+  (void)M;
+  (void)N;
+  (void)ld;
+  (void)h_dtype;
+  (void)G_D;
+  (void)g_E;
+  (void)dL_dH;
+  (void)opt;
+  return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,435 @@
+// Device-side control of the recursion: one single-block kernel per step
+// reduces the GEMM1 partials (in tile order, so the sums are deterministic),
+// applies the stop tests, computes c_n (Eq. mcwgamb) and the coefficients of
+// the cubic update (Eq. hpcp3), and sets the CUDA-graph WHILE condition, so
+// a whole solve runs without a host round trip.  Plus the small conversion
+// kernels around the loop.
+//
+// Stop rules (readings where the paper is silent, shared with the oracle):
+//   * ||D^2 - D||_F <= tol or Tr(D - D^2) <= tol (the paper's test);
+//   * 0/0 guard: Tr(D - D^2) <= 16 M u max(1, Tr D) ends the loop
+//     (in fixed-iteration mode the step becomes an identity step);
+//   * c_0 outside [0,1] reports GCP_ERR_ILL_CONDITIONED (Eqs. pmcpcons2-3);
+//   * FP64 stagnation: once R < 1e-8, two consecutive non-decreasing R;
+//   * split-precision floor: once R < 1e-2, a step that fails to reduce R
+//     by 4x ends the split phase (the products can go no further).
+#include "gcp_device.cuh"
+#include "gcp_internal.cuh"
+
+namespace gcp {
+
+namespace {
+constexpr int kCtlThreads = 256;
+
+__global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __restrict__ part,
+                                                              int ntiles, State* st, double* hist,
+                                                              Ctl ctl,
+                                                              cudaGraphConditionalHandle cond,
+                                                              int use_cond) {
+  __shared__ double red[32 * 5];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const double* p = part + (size_t)t * kPartFields;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] += p[k];
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  if (st->stopped) {
+    if (use_cond) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  // FP64 phase: v = (Tr D, Tr S, sum S o D, R^2, E).
+  // Split phase, on D = theta J + X and S = theta^2 J + Sigma (J the identity
+  // on the unpadded block): v = (Tr X, Tr Sigma, sum Sigma o X, R^2, E) and
+  //   Tr D = theta M + Tr X,  Tr S = theta^2 M + Tr Sigma,
+  //   sum S o D = theta^3 M + theta^2 Tr X + theta Tr Sigma + sum Sigma o X;
+  // den and num are formed from these parts directly, which keeps the O(M)
+  // constant terms out of the cancellation near convergence.
+  double T1, T2, T3, den, num;
+  if (ctl.phase == 1) {
+    const double th = st->theta, thb = 1.0 - th, Md = (double)ctl.M;
+    T1 = th * Md + v[0];
+    T2 = th * th * Md + v[1];
+    T3 = th * th * th * Md + th * th * v[0] + th * v[1] + v[2];
+    den = th * thb * Md + v[0] - v[1];
+    num = th * th * thb * Md + thb * v[1] - th * th * v[0] - v[2];
+  } else {
+    T1 = v[0];
+    T2 = v[1];
+    T3 = v[2];
+    den = T1 - T2;
+    num = T2 - T3;
+  }
+  const double R = sqrt(fmax(v[3], 0.0)), E = v[4];
+  st->T1 = T1;
+  st->T2 = T2;
+  st->T3 = T3;
+  st->R = R;
+  st->E = E;
+  const int n = st->n;
+  double* rec = nullptr;
+  if (hist && st->hist_n < ctl.hist_cap) {
+    rec = hist + (size_t)st->hist_n * GCP_HISTORY_FIELDS;
+    rec[0] = n;
+    rec[1] = T1;
+    rec[2] = T2;
+    rec[3] = T3;
+    rec[4] = R;
+    rec[5] = __longlong_as_double(0x7ff8000000000000ll);
+    rec[6] = E;
+    rec[7] = ctl.phase;
+    st->hist_n += 1;
+  }
+  // kind: 1 converged, 2 split-precision floor, 3 terminal
+  int stop = 0, status = GCP_OK, kind = 0;
+  if (st->timeout) {
+    stop = 1;
+    kind = 3;
+    status = GCP_ERR_TIMEOUT;
+  } else if (!isfinite(T1) || !isfinite(T2) || !isfinite(T3) || !isfinite(R)) {
+    stop = 1;
+    kind = 3;
+    status = GCP_ERR_NONFINITE;
+  } else if (ctl.fixed_iters > 0) {
+    if (n >= ctl.fixed_iters) {
+      stop = 1;
+      kind = 1;
+    }
+  } else {
+    const double crit = (ctl.stop == GCP_STOP_IDEMP_FRO) ? R : den;
+    if (crit <= ctl.tol) {
+      stop = 1;
+      kind = 1;
+    } else if (ctl.phase == 0 && R < 1e-8 && R >= st->Rp0 && st->Rp0 >= st->Rp1) {
+      stop = 1;
+      kind = 3;
+      status = (R <= ctl.tol) ? GCP_OK : GCP_ERR_NOT_CONVERGED;
+    } else if (ctl.phase == 1 && R < 1e-2 && R > 0.25 * st->Rp0) {
+      stop = 1;
+      kind = 2;
+    } else if (n >= ctl.max_iter) {
+      stop = 1;
+      kind = 3;
+      status = GCP_ERR_NOT_CONVERGED;
+    }
+  }
+  if (!stop) {
+    const double den_min = 16.0 * (double)ctl.M * ctl.u * fmax(1.0, T1);
+    if (den <= den_min) {
+      if (ctl.fixed_iters > 0) {
+        st->apply = 0;  // identity step
+        st->n = n + 1;
+        st->parity ^= 1;
+      } else if (R <= ctl.tol) {
+        stop = 1;
+        kind = 1;
+      } else if (ctl.phase == 1) {
+        stop = 1;
+        kind = 2;
+      } else {
+        stop = 1;
+        kind = 3;
+        status = GCP_ERR_NOT_CONVERGED;
+      }
+    } else {
+      const double c = num / den;
+      if (n == 0 && !(c >= 0.0 && c <= 1.0) && ctl.fixed_iters == 0) {
+        stop = 1;
+        kind = 3;
+        status = GCP_ERR_ILL_CONDITIONED;
+      } else {
+        st->c = c;
+        st->a = 1.0 - 2.0 * c;
+        st->b = 2.0 + 2.0 * c;
+        const double th = st->theta;
+        st->xshift = 2.0 * th * (1.0 - th) * (th - c);
+        st->apply = 1;
+        st->Rp1 = st->Rp0;
+        st->Rp0 = R;
+        st->n = n + 1;
+        if (ctl.phase == 1) st->n_lowp += 1;
+        st->parity ^= 1;
+        if (rec) rec[5] = c;
+      }
+    }
+  }
+  if (stop) {
+    st->stopped = 1;
+    st->apply = 0;
+    if (kind == 1) {
+      st->converged = 1;
+      st->status = GCP_OK;
+    } else if (kind == 3) {
+      st->terminal = 1;
+      st->status = status;
+    } else {
+      st->lowp_done = 1;
+      if (ctl.final_phase) {
+        st->terminal = 1;
+        st->status = GCP_ERR_NOT_CONVERGED;
+      }
+    }
+  }
+  if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+__global__ void state_init_kernel(State* st, int phase) {
+  // zero everything except the guess parameters written just before
+  st->n = 0;
+  st->n_lowp = 0;
+  st->stopped = 0;
+  st->status = GCP_OK;
+  st->apply = 0;
+  st->parity = 0;
+  st->phase = phase;
+  st->lowp_done = 0;
+  st->timeout = 0;
+  st->hist_n = 0;
+  st->converged = 0;
+  st->terminal = 0;
+  if (st->no_gap) {  // D = theta I, nothing to iterate
+    st->stopped = 1;
+    st->terminal = 1;
+    st->status = GCP_ERR_NO_GAP;
+  }
+  st->c = __longlong_as_double(0x7ff8000000000000ll);
+  st->a = st->b = 0.0;
+  st->T1 = st->T2 = st->T3 = st->R = st->E = 0.0;
+  st->Rp0 = st->Rp1 = INFINITY;
+  st->xshift = 0.0;
+}
+
+__global__ void phase_begin_kernel(State* st, int phase) {
+  // the FP64 refinement runs only after a split phase that reached its floor
+  const int go = st->lowp_done && !st->converged && !st->terminal && !st->no_gap;
+  st->stopped = go ? 0 : 1;
+  st->phase = phase;
+  st->parity = 0;
+  st->Rp0 = st->Rp1 = INFINITY;
+}
+
+template <typename O>
+__global__ void copy_out_f64_kernel(const double* __restrict__ b0, const double* __restrict__ b1,
+                                    const State* __restrict__ st, int M, int ld,
+                                    O* __restrict__ out, int ldo) {
+  const double* src = st->parity ? b1 : b0;
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+    out[(size_t)i * ldo + j] = (O)src[(size_t)i * ld + j];
+}
+
+template <typename O>
+__global__ void copy_out_x_kernel(const float* __restrict__ X0, const float* __restrict__ X1,
+                                  const State* __restrict__ st, int M, int ldx, O* __restrict__ out,
+                                  int ldo) {
+  const float* src = st->parity ? X1 : X0;
+  const double th = st->theta;
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    double v = (double)src[(size_t)i * ldx + j];
+    if (i == j) v += th;
+    out[(size_t)i * ldo + j] = (O)v;
+  }
+}
+
+__global__ void x_to_d64_kernel(const float* __restrict__ X0, const float* __restrict__ X1,
+                                const State* __restrict__ st, int M, int ldx, double* __restrict__ D,
+                                int ldd) {
+  const float* src = st->parity ? X1 : X0;
+  const double th = st->theta;
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    double v = (double)src[(size_t)i * ldx + j];
+    if (i == j) v += th;
+    D[(size_t)i * ldd + j] = v;
+  }
+}
+
+// Re-anchor Tr D to N after the FP32 split phase: D += ((N - Tr D)/M) I.
+// The recursion conserves whatever trace its input has; FP32 rounding of
+// the stored iterate moves it by O(sqrt(M) u_32) per step, and a trace off N
+// by delta leaves a stationary eigenvalue at delta, so ||D^2 - D|| could
+// never pass below |delta|.  A scalar shift keeps every eigenvector.
+__global__ void anchor_trace_kernel(double* __restrict__ D, int M, int ldd, int N) {
+  __shared__ double red[32];
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < M; i += blockDim.x) v[0] += D[(size_t)i * ldd + i];
+  block_sum<1>(v, red);
+  __shared__ double shift;
+  if (threadIdx.x == 0) shift = ((double)N - v[0]) / (double)M;
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) D[(size_t)i * ldd + i] += shift;
+}
+
+template <typename I, typename O>
+__global__ void convert_kernel(const I* __restrict__ in, int ldi, O* __restrict__ out, int ldo,
+                               int M) {
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+    out[(size_t)i * ldo + j] = (O)in[(size_t)i * ldi + j];
+}
+
+template <typename O>
+__global__ void fill_kernel(O* __restrict__ out, int M, int ldo, double diag) {
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+    out[(size_t)i * ldo + j] = (O)(i == j ? diag : 0.0);
+}
+
+template <typename I, bool BF16>
+__global__ void d_to_x_kernel(const I* __restrict__ D, int M, int ld, float* __restrict__ X,
+                              typename Split<BF16>::T* __restrict__ Xh,
+                              typename Split<BF16>::T* __restrict__ Xl, int Mp, float scale,
+                              double theta) {
+  const int i = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Mp; j += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (i < M && j < M) {
+      v = (double)D[(size_t)i * ld + j];
+      if (i == j) v -= theta;
+    }
+    const float x = (float)v;
+    const size_t o = (size_t)i * Mp + j;
+    X[o] = x;
+    typename Split<BF16>::T h, l;
+    Split<BF16>::split(x * scale, h, l);
+    Xh[o] = h;
+    Xl[o] = l;
+  }
+}
+
+inline dim3 row_grid(int cols, int rows) {
+  int gx = (cols + 255) / 256;
+  if (gx > 8) gx = 8;
+  return dim3(gx, rows);
+}
+}  // namespace
+
+void launch_control(const double* part, int ntiles, State* st, double* hist, Ctl ctl,
+                    unsigned long long cond_handle, int use_cond, cudaStream_t s) {
+  control_kernel<<<1, kCtlThreads, 0, s>>>(part, ntiles, st, hist, ctl,
+                                           (cudaGraphConditionalHandle)cond_handle, use_cond);
+}
+
+void launch_state_init(State* st, int phase, cudaStream_t s) {
+  state_init_kernel<<<1, 1, 0, s>>>(st, phase);
+}
+
+void launch_phase_begin(State* st, int phase, cudaStream_t s) {
+  phase_begin_kernel<<<1, 1, 0, s>>>(st, phase);
+}
+
+void launch_copy_out_f64(const double* b0, const double* b1, const State* st, int M, int ld,
+                         void* out, int out_f64, int ldo, cudaStream_t s) {
+  if (out_f64)
+    copy_out_f64_kernel<double><<<row_grid(M, M), 256, 0, s>>>(b0, b1, st, M, ld, (double*)out, ldo);
+  else
+    copy_out_f64_kernel<float><<<row_grid(M, M), 256, 0, s>>>(b0, b1, st, M, ld, (float*)out, ldo);
+}
+
+void launch_copy_out_x(const float* X0, const float* X1, const State* st, int M, int ldx,
+                       void* out, int out_f64, int ldo, cudaStream_t s) {
+  if (out_f64)
+    copy_out_x_kernel<double><<<row_grid(M, M), 256, 0, s>>>(X0, X1, st, M, ldx, (double*)out, ldo);
+  else
+    copy_out_x_kernel<float><<<row_grid(M, M), 256, 0, s>>>(X0, X1, st, M, ldx, (float*)out, ldo);
+}
+
+void launch_x_to_d64(const float* X0, const float* X1, State* st, int M, int ldx, double* D,
+                     int ldd, int N, cudaStream_t s) {
+  x_to_d64_kernel<<<row_grid(M, M), 256, 0, s>>>(X0, X1, st, M, ldx, D, ldd);
+  anchor_trace_kernel<<<1, 1024, 0, s>>>(D, M, ldd, N);
+}
+
+void launch_d_to_x(const void* D, int d_f64, int M, int ld, float* X, void* Xh, void* Xl, int Mp,
+                   int bf16, float split_scale, double theta, cudaStream_t s) {
+  const dim3 g = row_grid(Mp, Mp);
+  if (bf16) {
+    using T = Split<true>::T;
+    if (d_f64)
+      d_to_x_kernel<double, true><<<g, 256, 0, s>>>((const double*)D, M, ld, X, (T*)Xh, (T*)Xl, Mp,
+                                                   split_scale, theta);
+    else
+      d_to_x_kernel<float, true><<<g, 256, 0, s>>>((const float*)D, M, ld, X, (T*)Xh, (T*)Xl, Mp,
+                                                  split_scale, theta);
+  } else {
+    using T = Split<false>::T;
+    if (d_f64)
+      d_to_x_kernel<double, false><<<g, 256, 0, s>>>((const double*)D, M, ld, X, (T*)Xh, (T*)Xl,
+                                                    Mp, split_scale, theta);
+    else
+      d_to_x_kernel<float, false><<<g, 256, 0, s>>>((const float*)D, M, ld, X, (T*)Xh, (T*)Xl, Mp,
+                                                   split_scale, theta);
+  }
+}
+
+void launch_fill(const void*, void* out, int out_f64, int M, int ldo, double diag, cudaStream_t s) {
+  if (out_f64)
+    fill_kernel<double><<<row_grid(M, M), 256, 0, s>>>((double*)out, M, ldo, diag);
+  else
+    fill_kernel<float><<<row_grid(M, M), 256, 0, s>>>((float*)out, M, ldo, diag);
+}
+
+void launch_convert(const void* in, int in_f64, int ldi, void* out, int out_f64, int ldo, int M,
+                    cudaStream_t s) {
+  const dim3 g = row_grid(M, M);
+  if (in_f64 && out_f64)
+    convert_kernel<double, double><<<g, 256, 0, s>>>((const double*)in, ldi, (double*)out, ldo, M);
+  else if (in_f64)
+    convert_kernel<double, float><<<g, 256, 0, s>>>((const double*)in, ldi, (float*)out, ldo, M);
+  else if (out_f64)
+    convert_kernel<float, double><<<g, 256, 0, s>>>((const float*)in, ldi, (double*)out, ldo, M);
+  else
+    convert_kernel<float, float><<<g, 256, 0, s>>>((const float*)in, ldi, (float*)out, ldo, M);
+}
+
+}  // namespace gcp
+
+// ---- energy E = Tr(H D) = sum_ij D_ij H_ij of the returned D -------------
+namespace gcp {
+namespace {
+template <typename DT, typename HT>
+__global__ void __launch_bounds__(256) energy_kernel(const DT* __restrict__ D, int ldd,
+                                                     const HT* __restrict__ H, int ldh, int M,
+                                                     double* __restrict__ part) {
+  __shared__ double red[32];
+  double v[1] = {0.0};
+  const int warps = blockDim.x / 32;
+  const int gw = blockIdx.x * warps + (threadIdx.x >> 5), nw = gridDim.x * warps;
+  const int lane = threadIdx.x & 31;
+  for (int i = gw; i < M; i += nw) {
+    const DT* d = D + (size_t)i * ldd;
+    const HT* hr = H + (size_t)i * ldh;
+    for (int j = lane; j < M; j += 32) v[0] += (double)d[j] * (double)hr[j];
+  }
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+__global__ void energy_finalize_kernel(const double* __restrict__ part, int nb, State* st) {
+  if (threadIdx.x != 0) return;
+  double e = 0.0;
+  for (int b = 0; b < nb; ++b) e += part[b];
+  st->E = e;
+}
+}  // namespace
+
+void launch_energy(const void* D, int d_f64, int ldd, const void* H, int h_f64, int ldh, int M,
+                   double* part, State* st, cudaStream_t s) {
+  const int nb = guess_partial_blocks(M);
+  if (d_f64 && h_f64)
+    energy_kernel<double, double><<<nb, 256, 0, s>>>((const double*)D, ldd, (const double*)H, ldh,
+                                                    M, part);
+  else if (d_f64)
+    energy_kernel<double, float><<<nb, 256, 0, s>>>((const double*)D, ldd, (const float*)H, ldh, M,
+                                                   part);
+  else if (h_f64)
+    energy_kernel<float, double><<<nb, 256, 0, s>>>((const float*)D, ldd, (const double*)H, ldh, M,
+                                                   part);
+  else
+    energy_kernel<float, float><<<nb, 256, 0, s>>>((const float*)D, ldd, (const float*)H, ldh, M,
+                                                  part);
+  energy_finalize_kernel<<<1, 32, 0, s>>>(part, nb, st);
+}
+}  // namespace gcp

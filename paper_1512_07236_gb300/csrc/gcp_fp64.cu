@@ -1,0 +1,205 @@
+// FP64 products of one GCP step with fused epilogues (the plain FP64 GPU
+// path and the refinement engine of the mixed modes).
+//
+// GB300 runs FP64 on SIMT DFMA units at a small fraction of its tensor
+// rate, so these kernels are DFMA-bound at any practical size: register
+// tiles of RT x RT outputs per thread, operand slices staged in shared
+// memory.  Only tiles on or above the diagonal are computed (the products
+// of symmetric commuting matrices are symmetric) and each off-diagonal tile
+// is stored twice (direct and mirrored).
+//
+// GEMM1 (S = D D) epilogue, per tile, in FP64 (Eq. mcwgamb, Eq. mcw1b):
+//   T1 += D_ii, T2 += S_ii                 (diagonal tiles)
+//   T3 += w S_ij D_ij                      (Tr D^3 for symmetric D)
+//   R2 += w (S_ij - D_ij)^2                (||D^2 - D||_F^2, elementwise)
+//   E  += w D_ij H_ij                      (Tr H D)
+// with w = 2 for an off-diagonal tile (it stands for its mirror) and 1 on
+// the diagonal.  One record of partials per tile; the control kernel sums
+// them in tile order, so the result does not depend on scheduling.
+// GEMM2 (P = S D) epilogue: D_{n+1} = a D + b S - 2 P with a = 1 - 2c,
+// b = 2 + 2c (Eq. hpcp3 expanded).
+#include "gcp_device.cuh"
+#include "gcp_internal.cuh"
+
+namespace gcp {
+
+namespace {
+constexpr int kThreads = 256;
+constexpr int kBK = 16;
+
+__device__ __forceinline__ void tile_coords(int t, int T, int& bi, int& bj) {
+  int i = 0;
+  while (t >= T - i) {
+    t -= T - i;
+    ++i;
+  }
+  bi = i;
+  bj = i + t;
+}
+
+// acc[i][j] = sum_k A[m0 + ty + 16 i][k] * B[k][n0 + tx + 16 j] with A, B
+// symmetric, so both slices are row reads of the operands.
+template <int BT>
+__device__ __forceinline__ void f64_mainloop(const double* __restrict__ A,
+                                             const double* __restrict__ B, int M, int ld, int m0,
+                                             int n0, double (&acc)[BT / 16][BT / 16],
+                                             double (*As)[BT], double (*Bs)[BT]) {
+  constexpr int RT = BT / 16;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+#pragma unroll
+    for (int j = 0; j < RT; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < M; k0 += kBK) {
+    for (int e = threadIdx.x; e < kBK * BT; e += kThreads) {
+      const int k = e / BT, c = e % BT;
+      const int gk = k0 + k;
+      As[k][c] = (gk < M && m0 + c < M) ? A[(size_t)gk * ld + m0 + c] : 0.0;
+      Bs[k][c] = (gk < M && n0 + c < M) ? B[(size_t)gk * ld + n0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBK; ++k) {
+      double a[RT], b[RT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < RT; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int BT, typename HT>
+__global__ void __launch_bounds__(kThreads) f64_gemm1_kernel(const double* __restrict__ D,
+                                                             double* __restrict__ S, int M, int ld,
+                                                             const HT* __restrict__ H, int ldh,
+                                                             double* __restrict__ part,
+                                                             const State* __restrict__ st) {
+  if (st->stopped) return;
+  __shared__ double As[kBK][BT];
+  __shared__ double Bs[kBK][BT];
+  __shared__ double red[32 * 5];
+  constexpr int RT = BT / 16;
+  const int T = (M + BT - 1) / BT;
+  int bi, bj;
+  tile_coords(blockIdx.x, T, bi, bj);
+  const int m0 = bi * BT, n0 = bj * BT;
+  double acc[RT][RT];
+  f64_mainloop<BT>(D, D, M, ld, m0, n0, acc, As, Bs);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const double w = (bi == bj) ? 1.0 : 2.0;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    const int r = m0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (r < M && c < M) {
+        const double s = acc[i][j];
+        const double d = D[(size_t)r * ld + c];
+        if (r == c) {
+          v[0] += d;
+          v[1] += s;
+        }
+        v[2] += w * s * d;
+        v[3] += w * (s - d) * (s - d);
+        if (H) v[4] += w * d * (double)H[(size_t)r * ldh + c];
+        S[(size_t)r * ld + c] = s;
+        if (bi != bj) S[(size_t)c * ld + r] = s;
+      }
+    }
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    double* p = part + (size_t)blockIdx.x * kPartFields;
+    p[0] = v[0];
+    p[1] = v[1];
+    p[2] = v[2];
+    p[3] = v[3];
+    p[4] = v[4];
+    p[5] = 0.0;
+  }
+}
+
+template <int BT>
+__global__ void __launch_bounds__(kThreads) f64_gemm2_kernel(const double* __restrict__ S,
+                                                             const double* __restrict__ D,
+                                                             double* __restrict__ Dn, int M,
+                                                             int ld, const State* __restrict__ st) {
+  if (st->stopped) return;
+  __shared__ double As[kBK][BT];
+  __shared__ double Bs[kBK][BT];
+  constexpr int RT = BT / 16;
+  const int T = (M + BT - 1) / BT;
+  int bi, bj;
+  tile_coords(blockIdx.x, T, bi, bj);
+  const int m0 = bi * BT, n0 = bj * BT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool apply = st->apply != 0;
+  const double a = st->a, b = st->b;
+  double acc[RT][RT];
+  if (apply) {
+    f64_mainloop<BT>(S, D, M, ld, m0, n0, acc, As, Bs);
+  }
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    const int r = m0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (r < M && c < M) {
+        const size_t o = (size_t)r * ld + c;
+        const double d = D[o];
+        const double x = apply ? (a * d + b * S[o] - 2.0 * acc[i][j]) : d;
+        Dn[o] = x;
+        if (bi != bj) Dn[(size_t)c * ld + r] = x;
+      }
+    }
+  }
+}
+}  // namespace
+
+int f64_tile(int M) { return M <= 1024 ? 32 : 64; }
+
+int f64_num_tiles(int M) {
+  const int BT = f64_tile(M);
+  const int T = (M + BT - 1) / BT;
+  return T * (T + 1) / 2;
+}
+
+void launch_f64_gemm1(const double* D, double* S, int M, int ld, const void* H, int h_f64, int ldh,
+                      double* part, const State* st, cudaStream_t s) {
+  const int nt = f64_num_tiles(M);
+  if (f64_tile(M) == 32) {
+    if (h_f64 || !H)
+      f64_gemm1_kernel<32, double><<<nt, kThreads, 0, s>>>(D, S, M, ld, (const double*)H, ldh, part,
+                                                          st);
+    else
+      f64_gemm1_kernel<32, float><<<nt, kThreads, 0, s>>>(D, S, M, ld, (const float*)H, ldh, part,
+                                                         st);
+  } else {
+    if (h_f64 || !H)
+      f64_gemm1_kernel<64, double><<<nt, kThreads, 0, s>>>(D, S, M, ld, (const double*)H, ldh, part,
+                                                          st);
+    else
+      f64_gemm1_kernel<64, float><<<nt, kThreads, 0, s>>>(D, S, M, ld, (const float*)H, ldh, part,
+                                                         st);
+  }
+}
+
+void launch_f64_gemm2(const double* S, const double* D, double* Dn, int M, int ld,
+                      const State* st, cudaStream_t s) {
+  const int nt = f64_num_tiles(M);
+  if (f64_tile(M) == 32)
+    f64_gemm2_kernel<32><<<nt, kThreads, 0, s>>>(S, D, Dn, M, ld, st);
+  else
+    f64_gemm2_kernel<64><<<nt, kThreads, 0, s>>>(S, D, Dn, M, ld, st);
+}
+
+}  // namespace gcp

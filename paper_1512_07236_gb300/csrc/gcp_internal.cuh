@@ -1,0 +1,119 @@
+// Internal declarations shared by the translation units of libgcp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gcp.h"
+
+namespace gcp {
+
+constexpr double kU64 = 1.1102230246251565e-16;  // 2^-53
+
+// Device-resident solver state.  One instance per solve; written only by
+// the single-block control kernels, read by every kernel of an iteration.
+struct State {
+  int n;            // steps applied so far (all phases)
+  int n_lowp;       // steps applied in the split-precision phase
+  int stopped;      // 1 once the current phase has stopped
+  int status;       // gcp_status
+  int apply;        // the GEMM2 of this iteration applies an update
+  int parity;       // index of the ping-pong buffer holding the current iterate
+  int phase;        // 1 = split precision, 0 = FP64
+  int lowp_done;    // split-precision phase finished (stagnated or converged)
+  int no_gap;
+  int timeout;      // a bounded wait in a kernel gave up
+  int hist_n;
+  int converged;    // the stop test held
+  int terminal;     // stopped for good (max_iter, stagnation, hard error)
+  int pad_;
+  double c, a, b;           // c_n and the polynomial coefficients of D_{n+1}
+  double T1, T2, T3, R, E;  // traces of the last evaluated iterate
+  double Rp0, Rp1;          // residuals of the two previous evaluated iterates
+  double mu, beta2, hmin, hmax, theta;
+  double xshift;            // J coefficient of X+ (split phase)
+};
+
+// Scalar options every control kernel needs (passed by value).
+struct Ctl {
+  int M, N;
+  int stop;         // gcp_stop
+  int max_iter;
+  int fixed_iters;
+  int hist_cap;
+  int phase;        // 1 split precision, 0 FP64
+  int final_phase;  // this phase decides the final status
+  double tol;
+  double u;         // unit roundoff of the phase's state (den guard)
+};
+
+// Number of partial-sum fields written per GEMM1 tile.
+constexpr int kPartFields = 6;  // T1, T2, T3, R^2, E, spare
+
+// ---- guess (gcp_guess.cu) ------------------------------------------------
+int guess_partial_blocks(int M);
+// Gershgorin row bounds, trace, max|H_ii|: per-block partials (4 doubles).
+void launch_guess_reduce(const void* H, int h_f64, int M, int ld, double* part, cudaStream_t s);
+// Combine partials, compute mu, beta2, write into State.
+void launch_guess_finalize(const double* part, int nblocks, int M, int N, State* st,
+                           cudaStream_t s);
+// D0 = theta I + beta2 (mu I - H) (FP64 or FP32 out), padded area zero.
+void launch_guess_write_d(const void* H, int h_f64, int M, int ld, void* D, int d_f64, int ldd,
+                          int rows_pad, const State* st, cudaStream_t s);
+// X0 = D0 - theta J in FP32 plus its split halves (fp16 or bf16), Mp x Mp.
+void launch_guess_write_x(const void* H, int h_f64, int M, int ld, float* X, void* Xh, void* Xl,
+                          int Mp, int bf16, float split_scale, const State* st, cudaStream_t s);
+
+// ---- FP64 products (gcp_fp64.cu) -------------------------------------------
+int f64_tile(int M);
+int f64_num_tiles(int M);
+// S = D D over upper tiles, mirrored; epilogue partials per tile.
+void launch_f64_gemm1(const double* D, double* S, int M, int ld, const void* H, int h_f64, int ldh,
+                      double* part, const State* st, cudaStream_t s);
+// Dn = a D + b S - 2 S D over upper tiles, mirrored.
+void launch_f64_gemm2(const double* S, const double* D, double* Dn, int M, int ld,
+                      const State* st, cudaStream_t s);
+
+// ---- control (gcp_control.cu) --------------------------------------------
+void launch_control(const double* part, int ntiles, State* st, double* hist, Ctl ctl,
+                    unsigned long long cond_handle, int use_cond, cudaStream_t s);
+void launch_state_init(State* st, int phase, cudaStream_t s);
+void launch_phase_begin(State* st, int phase, cudaStream_t s);
+// D_out = buf[parity] converted to the output dtype (FP64 source).
+void launch_copy_out_f64(const double* buf0, const double* buf1, const State* st, int M, int ld,
+                         void* out, int out_f64, int ldo, cudaStream_t s);
+// D_out = theta J + X[parity] (FP32 source, shifted).
+void launch_copy_out_x(const float* X0, const float* X1, const State* st, int M, int ldx,
+                       void* out, int out_f64, int ldo, cudaStream_t s);
+// D64 = theta J + X[parity], then Tr D64 re-anchored to N.
+void launch_x_to_d64(const float* X0, const float* X1, State* st, int M, int ldx, double* D,
+                     int ldd, int N, cudaStream_t s);
+// E = sum_ij D_ij H_ij into State::E (per-block partials in `part`).
+void launch_energy(const void* D, int d_f64, int ldd, const void* H, int h_f64, int ldh, int M,
+                   double* part, State* st, cudaStream_t s);
+// Generic conversions for gcp_step.
+void launch_d_to_x(const void* D, int d_f64, int M, int ld, float* X, void* Xh, void* Xl, int Mp,
+                   int bf16, float split_scale, double theta, cudaStream_t s);
+void launch_fill(const void* val_src_unused, void* out, int out_f64, int M, int ldo, double diag,
+                 cudaStream_t s);
+void launch_convert(const void* in, int in_f64, int ldi, void* out, int out_f64, int ldo, int M,
+                    cudaStream_t s);
+
+// ---- tensor-core split products (gcp_tc.cu) -----------------------------
+struct TcOperands;  // opaque: tensor maps for one (hi, lo) pair
+int tc_pad(int M);
+int tc_num_tiles(int Mp);
+// Build tensor maps for a pair of split halves (Mp x Mp, row-major).
+int tc_make_operands(TcOperands** op, const void* hi, const void* lo, int Mp, int bf16,
+                     char* err, int errlen);
+void tc_free_operands(TcOperands* op);
+// Mode 1: Y = X X, Sigma = 2 theta X + Y, partials.  Mode 2: Z = X Sigma,
+// X+ update.  See gcp_tc.cu for the epilogue formulas.
+int tc_launch_gemm1(const TcOperands* opX, const float* X, float* Sig, void* Sh, void* Sl,
+                    int M, int Mp, const void* H, int h_f64, int ldh, double* part, State* st,
+                    int bf16, float split_scale, int* dev_err, cudaStream_t s);
+int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X, const float* Sig,
+                    float* Xn, void* Xnh, void* Xnl, int M, int Mp, State* st, int bf16,
+                    float split_scale, int* dev_err, cudaStream_t s);
+void tc_set_smem_attrs();
+
+}  // namespace gcp
