@@ -1,0 +1,335 @@
+"""Benchmark of the GCP solver on one GB300 (or N independent replicas).
+
+Workload (default): one dense symmetric H, M=8192, N=2048, H = Q diag(eps) Q^T
+with Q from the Householder QR of a seeded N(0,1) matrix, occupied levels
+uniform in [-1, -0.005] and virtual in [0.005, 1] (gap 0.01); mixed precision
+(split-FP16 tensor-core products, FP64 refinement) to ||D^2 - D||_F <= 1e-6.
+
+One step = one full solve (guess -> converged D -> energy).  `value` is the
+effective GCP rate, 4 M^3 flops per applied step (two dense products) over
+the solve time, in TFLOP/s.  Inputs (H is 512 MiB in FP64) exceed the 129 MB
+L2, so no flush is needed between steps.  Multi-GPU: independent replicas
+(each rank solves its own H), weak scaling, no collective on the data path.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample (a few purification steps of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M_DEFAULT, N_DEFAULT, GAP_DEFAULT = 8192, 2048, 0.01
+TOL = 1e-6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gcp", choices=["gcp", "reference"])
+    p.add_argument("--M", type=int, default=M_DEFAULT)
+    p.add_argument("--N", type=int, default=N_DEFAULT)
+    p.add_argument("--gap", type=float, default=GAP_DEFAULT)
+    p.add_argument("--prec", default="mixed_fp16")
+    p.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    p.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--cpu-iters", type=int, default=2)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_input(M, N, gap, seed, qr_backend="torch"):
+    from paper_1512_07236_gb300 import inputs
+    return inputs.rotated_spectrum(M, N, (-1.0, -gap / 2), (gap / 2, 1.0), seed=seed,
+                                   qr_backend=qr_backend)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(H, N, iters):
+    """The FP64 oracle as it stands, `iters` purification steps of the
+    workload; returns (seconds, applied steps)."""
+    from oracle import gcp_oracle as o
+    t0 = time.perf_counter()
+    r = o.solve(H, N, fixed_iters=iters, record=False)
+    return time.perf_counter() - t0, r["iters"]
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    M, N = args.M, args.N
+    H, eps, Q = make_input(M, N, args.gap, seed=2, qr_backend="numpy")
+    flops_step = 4.0 * M ** 3
+    for _ in range(args.warmup):
+        oracle_sample(H, N, 1)
+    times = []
+    for _ in range(args.steps):
+        t, n = oracle_sample(H, N, args.cpu_iters)
+        times.append(t / max(n, 1))
+    per_step = statistics.mean(times)
+    value = flops_step / per_step / 1e12
+    line = {
+        "impl": "reference", "metric": "GCP effective TFLOP/s (FP64 CPU oracle)",
+        "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"dense rotated spectrum M={M} N={N} gap={args.gap}",
+                   "M": M, "N": N, "gap": args.gap,
+                   "sample": f"{args.cpu_iters} purification steps per timed step"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
+                         "kind": "oracle",
+                         "sample": f"{args.cpu_iters} FP64 steps of M={M} (numpy, host BLAS)"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1512_07236_gb300 import gcp
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    M, N = args.M, args.N
+    H, eps, Q = make_input(M, N, args.gap, seed=2 + rank)
+    Ht = torch.from_numpy(H).to(dev)
+    D = torch.empty((M, M), dtype=torch.float64, device=dev)
+    solver = gcp.Solver()
+    stream = torch.cuda.current_stream()
+    opts = dict(prec=args.prec, tol=TOL, max_iter=100)
+
+    def solve_once():
+        return solver.solve(Ht, N, out=D, **opts)
+
+    # warm-up (graph capture on the first call)
+    for _ in range(args.warmup):
+        _, info = solve_once()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = []
+        for _ in range(args.steps):
+            _, info = solve_once()
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    iters = infos[-1]["iters"]
+    flops_step = 4.0 * M ** 3 * iters
+    value = world * flops_step * args.steps / (ms_total * 1e-3) / 1e12
+
+    # --- accuracy of the returned D against the exact projector (FP64) ----
+    acc = {}
+    if rank == 0:
+        Qo = torch.from_numpy(Q[:, :N]).to(dev)
+        Dref = Qo @ Qo.T
+        diff = D - Dref
+        acc = {
+            "fro_err_over_sqrtN": float(torch.linalg.norm(diff) / np.sqrt(N)),
+            "max_abs_err": float(diff.abs().max()),
+            "energy_rel_err": abs(infos[-1]["energy"] - float(eps[:N].sum())) / abs(float(eps[:N].sum())),
+            "trace_err": abs(float(torch.trace(D)) - N),
+            "idem_fro": infos[-1]["idem_fro"],
+        }
+        del Dref, diff, Qo
+
+    # --- dominant kernel: tensor-core GEMMs, timed alone with CUDA events --
+    split_prec = "bf16x3" if "bf16" in args.prec else "fp16x3"
+    roof = None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    fp16_note = "of measured" if "bf16_tflops" in peaks else "of fallback"
+    try:
+        solver.solve(Ht, N, out=D, **opts)
+        t1, t2 = solver.time_kernels(M, N, prec=split_prec, reps=5)
+        alg = 2.0 * M ** 3  # dense-equivalent flops of one product
+        achieved = 2 * alg / ((t1 + t2) * 1e-3) / 1e12
+        # executed tensor flops: 3 products over the computed upper tiles
+        Mp = ((M + 255) // 256) * 256
+        ntiles = sum(min(2 * j + 2, Mp // 128) for j in range(Mp // 256))
+        executed = 3 * 2.0 * ntiles * 128 * 256 * Mp
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": achieved / bf16_peak, "traffic": None,
+                "kernel": "tc_gemm_kernel (GEMM1 + GEMM2 of one step)",
+                "ms_gemm1": t1, "ms_gemm2": t2,
+                "executed_tflops": 2 * executed / ((t1 + t2) * 1e-3) / 1e12,
+                "peak_note": f"bf16 dense burst {fp16_note} (fp16 has the same nominal rate)"}
+    except Exception as e:  # noqa: BLE001
+        roof = {"bound": "tensor", "achieved": None, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "error": str(e)}
+
+    # --- plain FP64 GPU path: time to the same tolerance -------------------
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        D64 = torch.empty_like(D)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, i64 = solver.solve(Ht, N, out=D64, prec="fp64", tol=TOL, max_iter=100)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms": a.elapsed_time(b), "iters": i64["iters"], "status": i64["status"],
+                "idem_fro": i64["idem_fro"]}
+        del D64
+
+    # --- end to end through the C ABI with host buffers --------------------
+    Hh = torch.from_numpy(H).pin_memory()
+    Dh = torch.empty((M, M), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Ht.copy_(Hh, non_blocking=True)
+        _, info = solver.solve(Ht, N, out=D, **opts)
+        Dh.copy_(D, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    e2e_value = world * flops_step * args.steps / (ms_e2e * 1e-3) / 1e12
+
+    # --- CPU oracle baseline on a bounded sample ---------------------------
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        t, n = oracle_sample(H, N, args.cpu_iters)
+        cpu = {"value": 4.0 * M ** 3 * n / t / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(),
+               "kind": "oracle",
+               "sample": f"{n} FP64 purification steps of M={M} (numpy + host BLAS), "
+                         f"{t:.1f} s"}
+
+    # kernel launches per solve: guess 4, per WHILE body 6 (two steps),
+    # transition 3, copy-out 1, energy 2
+    lp, l64 = infos[-1]["iters_lowp"], infos[-1]["iters_fp64"]
+    bodies = (lp + 2) // 2 + ((l64 + 2) // 2 if "mixed" in args.prec or args.prec == "fp64" else 0)
+    launches = args.steps * (4 + 6 * bodies + 3 + 1 + 2)
+
+    if rank == 0:
+        line = {
+            "metric": "GCP effective TFLOP/s (dense-equivalent 4 M^3 per step) to ||D^2-D||_F<=1e-6",
+            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp16x3+f64",
+            "data": "synthetic",
+            "config": {"workload": f"dense rotated spectrum M={M} N={N} gap={args.gap}, "
+                                   f"{args.prec}, tol {TOL}",
+                       "M": M, "N": N, "gap": args.gap, "prec": args.prec,
+                       "iters": iters, "iters_lowp": lp, "iters_fp64": l64,
+                       "l2": "inputs larger than L2 (H 512 MiB FP64)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_tol_s": ms_step * 1e-3,
+            "fp64_gpu_path": fp64,
+            "speedup_vs_fp64_gpu": (fp64["ms"] / ms_step) if fp64 else None,
+            "accuracy": acc,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": M * M * 8, "d2h_bytes_per_step": M * M * 8},
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "status": infos[-1]["status"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -165,6 +165,17 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
 gcp_status gcp_backward(void* handle, const void* H, int M, int N, int ld, int h_dtype,
                         const void* G_D, double g_E, void* dL_dH, const gcp_options* opt);
 
+/* Diagnostic (no counterpart in the paper): time the two products of one
+ * step on the workspace left by the last gcp_solve on this handle (same M;
+ * `prec` GCP_FP64 times the FP64 kernels, GCP_FP16X3/GCP_BF16X3 the
+ * tensor-core ones and needs a prior split or mixed solve).  Each kernel is
+ * launched `reps` times on opt->stream, bracketed by CUDA events;
+ * ms (host, 2 doubles) receives the mean duration of GEMM1 and GEMM2 in
+ * milliseconds.  The workspace iterate is overwritten: solve again before
+ * reading results. */
+gcp_status gcp_time_kernels(void* handle, int M, int N, int prec, int reps, double* ms,
+                            const gcp_options* opt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -197,6 +197,7 @@ struct SolveArgs {
 
 Ctl make_ctl(const SolveArgs& a, int phase, int final_phase) {
   Ctl c{};
+  c.endgame = is_split(a.o.prec) ? 1 : 0;
   c.M = a.M;
   c.N = a.N;
   c.stop = a.o.stop;
@@ -308,8 +309,10 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
     }
   }
   if (mixed) {
-    launch_phase_begin(h->st, 0, s);
+    // convert the split iterate (buffer chosen by the parity) before the
+    // FP64 phase resets the parity to its own buffer 0
     launch_x_to_d64(h->X[0], h->X[1], h->st, M, h->mp, h->D64[0], M, N, s);
+    launch_phase_begin(h->st, 0, s);
   }
   if (!split || mixed) {
     const Ctl ctl = make_ctl(a, 0, 1);
@@ -665,6 +668,75 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
   (void)dL_dH;
   (void)opt;
   return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: not built yet");
+}
+
+gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* ms,
+                            const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  if (M <= 0 || N <= 0 || N >= M || reps <= 0 || !ms)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_time_kernels: bad arguments");
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const bool split = prec == GCP_FP16X3 || prec == GCP_BF16X3;
+  if (split) {
+    if (h->mp != tc_pad(M) || h->tc_bf16 != (prec == GCP_BF16X3) || !h->opS)
+      return fail(h, GCP_ERR_NO_CHECKPOINT, "gcp_time_kernels: no split workspace of this size");
+  } else if (prec == GCP_FP64) {
+    if (h->m64 < M) return fail(h, GCP_ERR_NO_CHECKPOINT, "gcp_time_kernels: no FP64 workspace");
+  } else {
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_time_kernels: prec must be FP64, FP16X3 or BF16X3");
+  }
+  // a live state: apply = 1 with c = 1/2 (McWeeny coefficients)
+  State init;
+  memset(&init, 0, sizeof init);
+  init.theta = (double)N / (double)M;
+  init.apply = 1;
+  init.c = 0.5;
+  init.a = 0.0;
+  init.b = 3.0;
+  init.xshift = 2.0 * init.theta * (1.0 - init.theta) * (init.theta - 0.5);
+  CK(cudaMemcpyAsync(h->st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e[4];
+  for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&e[i]));
+  const int Mp = h->mp, bf = h->tc_bf16;
+  CK(cudaEventRecord(e[0], s));
+  for (int r = 0; r < reps; ++r) {
+    if (split) {
+      if (tc_launch_gemm1(h->opX[0], h->X[0], h->Sig, h->Sh, h->Sl, M, Mp, nullptr, 1, M, h->part,
+                          h->st, bf, kSplitScale, nullptr, s))
+        return fail(h, GCP_ERR_CUDA, "GEMM1 launch failed");
+    } else {
+      launch_f64_gemm1(h->D64[0], h->S64, M, M, nullptr, 1, M, h->part, h->st, s);
+    }
+  }
+  CK(cudaEventRecord(e[1], s));
+  CK(cudaEventRecord(e[2], s));
+  for (int r = 0; r < reps; ++r) {
+    if (split) {
+      if (tc_launch_gemm2(h->opS, h->opX[0], h->X[0], h->Sig, h->X[1], h->Xh[1], h->Xl[1], M, Mp,
+                          h->st, bf, kSplitScale, nullptr, s))
+        return fail(h, GCP_ERR_CUDA, "GEMM2 launch failed");
+    } else {
+      launch_f64_gemm2(h->S64, h->D64[0], h->D64[1], M, M, h->st, s);
+    }
+  }
+  CK(cudaEventRecord(e[3], s));
+  CK(cudaEventSynchronize(e[3]));
+  float t1 = 0.f, t2 = 0.f;
+  CK(cudaEventElapsedTime(&t1, e[0], e[1]));
+  CK(cudaEventElapsedTime(&t2, e[2], e[3]));
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+  ms[0] = t1 / reps;
+  ms[1] = t2 / reps;
+  State hs;
+  CK(cudaMemcpy(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost));
+  if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");
+  return GCP_OK;
 }
 
 }  // extern "C"

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
       kind = 3;
       status = (R <= ctl.tol) ? GCP_OK : GCP_ERR_NOT_CONVERGED;
     } else if (ctl.phase == 1 && R < 1e-2 && R > 0.25 * st->Rp0) {
+      // the split products can go no further: the residual stalls
       stop = 1;
       kind = 2;
     } else if (n >= ctl.max_iter) {
@@ -114,9 +115,24 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
       status = GCP_ERR_NOT_CONVERGED;
     }
   }
+  // Endgame of the split and refinement phases (ctl.endgame): once
+  // R < 0.05 every eigenvalue of D lies within ~R of 0 or 1, and c is set
+  // to 1/2, the McWeeny step (Eq. mcweeny3) that HPCP itself reaches as
+  // gamma -> 0.  The quotient of Eq. mcwgamb would be a ratio of two
+  // vanishing traces polluted by the rounding of the tensor-core products;
+  // the McWeeny step needs neither, and because it does not conserve the
+  // trace it also removes the rounding drift of Tr D (the eigenvalues go to
+  // exactly 0 or 1).  The same switch applies while that drift is not small
+  // against Tr(D - D^2).  The plain FP64 path keeps the oracle's rule.
+  const bool mcw = ctl.endgame && ctl.fixed_iters == 0 &&
+                   (R < 0.05 || fabs(T1 - (double)ctl.N) > 0.05 * fabs(den));
   if (!stop) {
-    const double den_min = 16.0 * (double)ctl.M * ctl.u * fmax(1.0, T1);
-    if (den <= den_min) {
+    // 0/0 guard.  FP64: 16 M u max(1, Tr D) (as in the oracle).  Split phase:
+    // the noise of den is set by the FP32 rounding of the O(1) diagonal,
+    // 16 sqrt(M) u_32.
+    const double den_min = ctl.phase == 1 ? 16.0 * sqrt((double)ctl.M) * ctl.u
+                                          : 16.0 * (double)ctl.M * ctl.u * fmax(1.0, T1);
+    if (den <= den_min && !mcw) {
       if (ctl.fixed_iters > 0) {
         st->apply = 0;  // identity step
         st->n = n + 1;
@@ -133,11 +149,31 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
         status = GCP_ERR_NOT_CONVERGED;
       }
     } else {
-      const double c = num / den;
+      // Split phase (before the endgame): c also absorbs the FP32 rounding
+      // drift of the trace, c = (num + (Tr D - N)/2) / den, so that
+      // Tr D_{n+1} = N for the traces as computed (exact arithmetic gives
+      // Tr D_n = N and the plain Eq. mcwgamb).  FP64: Eq. mcwgamb.
+      const double c = mcw ? 0.5
+                           : (ctl.phase == 1 ? (num + 0.5 * (T1 - (double)ctl.N)) / den
+                                             : num / den);
       if (n == 0 && !(c >= 0.0 && c <= 1.0) && ctl.fixed_iters == 0) {
         stop = 1;
         kind = 3;
         status = GCP_ERR_ILL_CONDITIONED;
+      } else if (ctl.endgame && n > 0 && !(c >= -0.05 && c <= 1.05) && ctl.fixed_iters == 0) {
+        // c left the stable domain (rounding noise): McWeeny step instead
+        st->c = 0.5;
+        st->a = 0.0;
+        st->b = 3.0;
+        const double th = st->theta;
+        st->xshift = 2.0 * th * (1.0 - th) * (th - 0.5);
+        st->apply = 1;
+        st->Rp1 = st->Rp0;
+        st->Rp0 = R;
+        st->n = n + 1;
+        if (ctl.phase == 1) st->n_lowp += 1;
+        st->parity ^= 1;
+        if (rec) rec[5] = 0.5;
       } else {
         st->c = c;
         st->a = 1.0 - 2.0 * c;
@@ -240,7 +276,8 @@ __global__ void x_to_d64_kernel(const float* __restrict__ X0, const float* __res
   const double th = st->theta;
   const int i = blockIdx.y;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-    double v = (double)src[(size_t)i * ldx + j];
+    // upper-triangle value for both (i, j) and (j, i): exactly symmetric
+    double v = (double)src[(size_t)(i < j ? i : j) * ldx + (i < j ? j : i)];
     if (i == j) v += th;
     D[(size_t)i * ldd + j] = v;
   }

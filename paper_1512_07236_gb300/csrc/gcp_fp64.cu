@@ -5,16 +5,17 @@
 // rate, so these kernels are DFMA-bound at any practical size: register
 // tiles of RT x RT outputs per thread, operand slices staged in shared
 // memory.  Only tiles on or above the diagonal are computed (the products
-// of symmetric commuting matrices are symmetric) and each off-diagonal tile
-// is stored twice (direct and mirrored).
+// of symmetric commuting matrices are symmetric); every element above the
+// diagonal is stored twice (direct and mirrored), so the results are exactly
+// symmetric.
 //
 // GEMM1 (S = D D) epilogue, per tile, in FP64 (Eq. mcwgamb, Eq. mcw1b):
 //   T1 += D_ii, T2 += S_ii                 (diagonal tiles)
 //   T3 += w S_ij D_ij                      (Tr D^3 for symmetric D)
 //   R2 += w (S_ij - D_ij)^2                (||D^2 - D||_F^2, elementwise)
 //   E  += w D_ij H_ij                      (Tr H D)
-// with w = 2 for an off-diagonal tile (it stands for its mirror) and 1 on
-// the diagonal.  One record of partials per tile; the control kernel sums
+// over the upper triangle, with w = 2 above the diagonal (the element
+// stands for its mirror) and 1 on it.  One record of partials per tile; the control kernel sums
 // them in tile order, so the result does not depend on scheduling.
 // GEMM2 (P = S D) epilogue: D_{n+1} = a D + b S - 2 P with a = 1 - 2c,
 // b = 2 + 2c (Eq. hpcp3 expanded).
@@ -92,7 +93,6 @@ __global__ void __launch_bounds__(kThreads) f64_gemm1_kernel(const double* __res
   double acc[RT][RT];
   f64_mainloop<BT>(D, D, M, ld, m0, n0, acc, As, Bs);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const double w = (bi == bj) ? 1.0 : 2.0;
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int i = 0; i < RT; ++i) {
@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(kThreads) f64_gemm1_kernel(const double* __res
 #pragma unroll
     for (int j = 0; j < RT; ++j) {
       const int c = n0 + tx + 16 * j;
-      if (r < M && c < M) {
+      // upper triangle only (weight 2 stands for the mirror), so the
+      // stored result is exactly symmetric
+      if (r < M && c < M && c >= r) {
+        const double w = (c == r) ? 1.0 : 2.0;
         const double s = acc[i][j];
         const double d = D[(size_t)r * ld + c];
         if (r == c) {
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) f64_gemm1_kernel(const double* __res
         v[3] += w * (s - d) * (s - d);
         if (H) v[4] += w * d * (double)H[(size_t)r * ldh + c];
         S[(size_t)r * ld + c] = s;
-        if (bi != bj) S[(size_t)c * ld + r] = s;
+        if (c != r) S[(size_t)c * ld + r] = s;
       }
     }
   }
@@ -153,12 +156,12 @@ __global__ void __launch_bounds__(kThreads) f64_gemm2_kernel(const double* __res
 #pragma unroll
     for (int j = 0; j < RT; ++j) {
       const int c = n0 + tx + 16 * j;
-      if (r < M && c < M) {
+      if (r < M && c < M && c >= r) {
         const size_t o = (size_t)r * ld + c;
         const double d = D[o];
         const double x = apply ? (a * d + b * S[o] - 2.0 * acc[i][j]) : d;
         Dn[o] = x;
-        if (bi != bj) Dn[(size_t)c * ld + r] = x;
+        if (c != r) Dn[(size_t)c * ld + r] = x;
       }
     }
   }

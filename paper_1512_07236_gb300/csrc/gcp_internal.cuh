@@ -42,6 +42,7 @@ struct Ctl {
   int hist_cap;
   int phase;        // 1 split precision, 0 FP64
   int final_phase;  // this phase decides the final status
+  int endgame;      // McWeeny endgame (split and refinement phases only)
   double tol;
   double u;         // unit roundoff of the phase's state (den guard)
 };

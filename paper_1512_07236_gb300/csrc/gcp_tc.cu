@@ -348,7 +348,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       float o[16];
       if (MODE == 1) {
-        const float w = diag_blk ? 1.f : 2.f;
         float p2 = 0.f, p3 = 0.f, p4 = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -356,6 +355,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float sg = fmaf(f2th, x[k], y);  // Sigma = 2 theta X + Y
           o[k] = sg;
           const int c = c0 + k;
+          // weight: an element above the diagonal stands for its mirror too;
+          // in a diagonal block only the upper triangle is kept
+          const float w = diag_blk ? (c > row ? 2.f : (c == row ? 1.f : 0.f)) : 2.f;
           const bool on_diag = diag_blk && (c == row) && in_m;
           const float e = sg - x[k] - (on_diag ? thtb : 0.f);  // (S - D)_ij
           p2 = fmaf(w * sg, x[k], p2);
@@ -396,31 +398,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
       }
-      // direct store: FP32 + halves
-      {
+      // stores: FP32 + halves.  The result is made exactly symmetric: in a
+      // diagonal block only elements on or above the diagonal are written,
+      // each also to its mirror position.
+      HT h[16], l[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) Split<BF16>::split(o[k] * ep.split_scale, h[k], l[k]);
+      if (diag_blk) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int c = c0 + k;
+          if (c < row) continue;
+          const size_t d0 = (size_t)row * Mp + c, mo = (size_t)c * Mp + row;
+          ep.out[d0] = o[k];
+          reinterpret_cast<HT*>(ep.out_h)[d0] = h[k];
+          reinterpret_cast<HT*>(ep.out_l)[d0] = l[k];
+          if (c > row) {
+            ep.out[mo] = o[k];
+            reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
+            reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
+          }
+        }
+      } else {
         float4* po = reinterpret_cast<float4*>(ep.out + rowoff);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           po[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-        HT h[16], l[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) Split<BF16>::split(o[k] * ep.split_scale, h[k], l[k]);
         uint4* ph = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_h) + rowoff);
         uint4* pl = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_l) + rowoff);
         ph[0] = *reinterpret_cast<const uint4*>(&h[0]);
         ph[1] = *reinterpret_cast<const uint4*>(&h[8]);
         pl[0] = *reinterpret_cast<const uint4*>(&l[0]);
         pl[1] = *reinterpret_cast<const uint4*>(&l[8]);
-        if (!diag_blk) {
-          // mirror: element (row, c) -> (c, row); lanes hold consecutive rows,
-          // so each of these stores is one coalesced segment per warp
+        // mirror: element (row, c) -> (c, row); lanes hold consecutive rows,
+        // so each of these stores is one coalesced segment per warp
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const size_t mo = (size_t)(c0 + k) * Mp + row;
-            ep.out[mo] = o[k];
-            reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
-            reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
-          }
+        for (int k = 0; k < 16; ++k) {
+          const size_t mo = (size_t)(c0 + k) * Mp + row;
+          ep.out[mo] = o[k];
+          reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
+          reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
         }
       }
     }

@@ -26,7 +26,7 @@ STOPS = {"idem_fro": 0, "trace": 1}
 HISTORY_FIELDS = 8
 EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destroy",
            "gcp_last_error", "gcp_init_guess", "gcp_step", "gcp_solve", "gcp_get_history",
-           "gcp_solve_batched", "gcp_backward")
+           "gcp_solve_batched", "gcp_backward", "gcp_time_kernels")
 
 
 class Options(C.Structure):
@@ -84,8 +84,9 @@ def load_library(path: str = LIB_PATH):
                                           C.POINTER(ip), ip, C.POINTER(vp), ip,
                                           C.POINTER(Result), C.POINTER(Options)]
         lib.gcp_backward.argtypes = [vp, vp, ip, ip, ip, ip, vp, dp, vp, C.POINTER(Options)]
+        lib.gcp_time_kernels.argtypes = [vp, ip, ip, ip, ip, C.POINTER(dp), C.POINTER(Options)]
         for name in ("gcp_create", "gcp_destroy", "gcp_init_guess", "gcp_step", "gcp_solve",
-                     "gcp_get_history", "gcp_solve_batched", "gcp_backward"):
+                     "gcp_get_history", "gcp_solve_batched", "gcp_backward", "gcp_time_kernels"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -200,6 +201,16 @@ class Solver:
         info = res.as_dict()
         info["status_code"] = st
         return out, info
+
+    def time_kernels(self, M, N, prec="fp16x3", reps=10):
+        """Mean duration (ms) of GEMM1 and GEMM2 of one step, CUDA events on
+        the current stream; needs a prior solve of size M on this handle."""
+        ms = (C.c_double * 2)()
+        p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        o = make_options()
+        self._check(self.lib.gcp_time_kernels(self.h, int(M), int(N), p, int(reps), ms,
+                                              C.byref(o)))
+        return ms[0], ms[1]
 
     def history(self, cap=1000):
         buf = (C.c_double * (cap * HISTORY_FIELDS))()

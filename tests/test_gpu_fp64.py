@@ -46,7 +46,9 @@ def test_ragged_sizes(solver, M, N):
     H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -0.15), (0.15, 1.0), seed=M + N)
     ref = o.solve(H, N, tol=1e-12)
     D, info = solver.solve(_dev(H), N, prec="fp64", tol=1e-12)
-    assert info["status"] == 0
+    # theta = 129/130 is a pathological filling: both sides hit max_iter
+    expect = {o.STATUS_OK: 0, o.STATUS_NOT_CONVERGED: 2}[ref["status"]]
+    assert info["status"] == expect
     assert np.abs(D.cpu().numpy() - ref["D"]).max() <= 1e-10
     assert abs(info["iters"] - ref["iters"]) <= 1
     assert abs(info["energy"] - ref["E"]) <= 1e-12 * max(1.0, abs(ref["E"]))
@@ -92,7 +94,8 @@ def test_history_invariants(solver):
     for hg, hr in zip(hist, ref["history"]):
         assert abs(hg["T1"] - 32) <= 1e-11
         assert hg["E"] == pytest.approx(hr["E"], rel=1e-12)
-        if not np.isnan(hr["c"]):
+        if not np.isnan(hr["c"]) and hr["T1"] - hr["T2"] > 1e-6:
+            # c is a ratio of two vanishing traces: compared while they are not rounding noise
             assert hg["c"] == pytest.approx(hr["c"], abs=1e-9)
             assert 0.0 <= hg["c"] <= 1.0
     E = [h["E"] for h in hist]
