@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     p.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-iters", type=int, default=2)
+    p.add_argument("--no-graph", action="store_true",
+                   help="host-driven loop (same kernels, one launch each; for launch lists)")
     return p.parse_args()
 
 
@@ -180,7 +182,7 @@ def main():
     D = torch.empty((M, M), dtype=torch.float64, device=dev)
     solver = gcp.Solver()
     stream = torch.cuda.current_stream()
-    opts = dict(prec=args.prec, tol=TOL, max_iter=100)
+    opts = dict(prec=args.prec, tol=TOL, max_iter=100, use_graph=not args.no_graph)
 
     def solve_once():
         return solver.solve(Ht, N, out=D, **opts)
@@ -295,10 +297,10 @@ def main():
                          f"{t:.1f} s"}
 
     # kernel launches per solve: guess 4, per WHILE body 6 (two steps),
-    # transition 3, copy-out 1, energy 2
+    # transition 2, copy-out 1, energy 2
     lp, l64 = infos[-1]["iters_lowp"], infos[-1]["iters_fp64"]
     bodies = (lp + 2) // 2 + ((l64 + 2) // 2 if "mixed" in args.prec or args.prec == "fp64" else 0)
-    launches = args.steps * (4 + 6 * bodies + 3 + 1 + 2)
+    launches = args.steps * (4 + 6 * bodies + 2 + 1 + 2)
 
     if rank == 0:
         line = {

@@ -311,7 +311,7 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
   if (mixed) {
     // convert the split iterate (buffer chosen by the parity) before the
     // FP64 phase resets the parity to its own buffer 0
-    launch_x_to_d64(h->X[0], h->X[1], h->st, M, h->mp, h->D64[0], M, N, s);
+    launch_x_to_d64(h->X[0], h->X[1], h->st, M, h->mp, h->D64[0], M, s);
     launch_phase_begin(h->st, 0, s);
   }
   if (!split || mixed) {

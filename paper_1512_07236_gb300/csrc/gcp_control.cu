@@ -283,22 +283,6 @@ __global__ void x_to_d64_kernel(const float* __restrict__ X0, const float* __res
   }
 }
 
-// Re-anchor Tr D to N after the FP32 split phase: D += ((N - Tr D)/M) I.
-// The recursion conserves whatever trace its input has; FP32 rounding of
-// the stored iterate moves it by O(sqrt(M) u_32) per step, and a trace off N
-// by delta leaves a stationary eigenvalue at delta, so ||D^2 - D|| could
-// never pass below |delta|.  A scalar shift keeps every eigenvector.
-__global__ void anchor_trace_kernel(double* __restrict__ D, int M, int ldd, int N) {
-  __shared__ double red[32];
-  double v[1] = {0.0};
-  for (int i = threadIdx.x; i < M; i += blockDim.x) v[0] += D[(size_t)i * ldd + i];
-  block_sum<1>(v, red);
-  __shared__ double shift;
-  if (threadIdx.x == 0) shift = ((double)N - v[0]) / (double)M;
-  __syncthreads();
-  for (int i = threadIdx.x; i < M; i += blockDim.x) D[(size_t)i * ldd + i] += shift;
-}
-
 template <typename I, typename O>
 __global__ void convert_kernel(const I* __restrict__ in, int ldi, O* __restrict__ out, int ldo,
                                int M) {
@@ -374,9 +358,8 @@ void launch_copy_out_x(const float* X0, const float* X1, const State* st, int M,
 }
 
 void launch_x_to_d64(const float* X0, const float* X1, State* st, int M, int ldx, double* D,
-                     int ldd, int N, cudaStream_t s) {
+                     int ldd, cudaStream_t s) {
   x_to_d64_kernel<<<row_grid(M, M), 256, 0, s>>>(X0, X1, st, M, ldx, D, ldd);
-  anchor_trace_kernel<<<1, 1024, 0, s>>>(D, M, ldd, N);
 }
 
 void launch_d_to_x(const void* D, int d_f64, int M, int ld, float* X, void* Xh, void* Xl, int Mp,

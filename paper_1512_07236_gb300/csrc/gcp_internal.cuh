@@ -85,9 +85,9 @@ void launch_copy_out_f64(const double* buf0, const double* buf1, const State* st
 // D_out = theta J + X[parity] (FP32 source, shifted).
 void launch_copy_out_x(const float* X0, const float* X1, const State* st, int M, int ldx,
                        void* out, int out_f64, int ldo, cudaStream_t s);
-// D64 = theta J + X[parity], then Tr D64 re-anchored to N.
+// D64 = theta J + X[parity] (upper triangle mirrored).
 void launch_x_to_d64(const float* X0, const float* X1, State* st, int M, int ldx, double* D,
-                     int ldd, int N, cudaStream_t s);
+                     int ldd, cudaStream_t s);
 // E = sum_ij D_ij H_ij into State::E (per-block partials in `part`).
 void launch_energy(const void* D, int d_f64, int ldd, const void* H, int h_f64, int ldh, int M,
                    double* part, State* st, cudaStream_t s);

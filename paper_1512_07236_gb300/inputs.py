@@ -57,9 +57,13 @@ def haar_like_q(M: int, seed: int, qr_backend: str = "numpy") -> np.ndarray:
         return Q
     import torch
 
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    Qt, _ = torch.linalg.qr(torch.from_numpy(A).to(dev))
-    return Qt.cpu().numpy()
+    At = torch.from_numpy(A)
+    if torch.cuda.is_available():
+        try:
+            return torch.linalg.qr(At.cuda())[0].cpu().numpy()
+        except RuntimeError:
+            pass  # the CUDA linear-algebra library may be unloadable (e.g. under a profiler)
+    return torch.linalg.qr(At)[0].numpy()
 
 
 def _two_band_eigs(rng, M, N, occ, virt):
