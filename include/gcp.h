@@ -165,6 +165,24 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
 gcp_status gcp_backward(void* handle, const void* H, int M, int N, int ld, int h_dtype,
                         const void* G_D, double g_E, void* dL_dH, const gcp_options* opt);
 
+/* Allocation-free FP64 solve (the paper has no counterpart: this is a
+ * deployment variant of gcp_solve).  For callers that must not allocate
+ * device memory while solving -- a program whose memory pool already holds
+ * the GPU's memory, a latency-bound loop that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, or code that cannot keep a handle.
+ * Same arguments and FP64 arithmetic as gcp_solve with opt->prec = GCP_FP64
+ * (other precisions and history return GCP_ERR_UNSUPPORTED), but no handle:
+ * the workspace is one fixed file-scope device array of 6.3 MB, so
+ * M <= 512 (larger M returns GCP_ERR_INVALID_ARG with a message in err).
+ * The array is shared by every call on a device and keeps the previous
+ * call's contents; calls whose GPU work overlaps race on it, so order them.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture).  err (host, may be NULL): errlen bytes for a
+ * one-line message.  Synchronous at exit like gcp_solve. */
+gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int h_dtype, void* D_out,
+                             int ldd, int d_dtype, gcp_result* res, const gcp_options* opt,
+                             char* err, int errlen);
+
 /* Diagnostic (no counterpart in the paper): time the two products of one
  * step on the workspace left by the last gcp_solve on this handle (same M;
  * `prec` GCP_FP64 times the FP64 kernels, GCP_FP16X3/GCP_BF16X3 the

@@ -26,7 +26,7 @@ STOPS = {"idem_fro": 0, "trace": 1}
 HISTORY_FIELDS = 8
 EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destroy",
            "gcp_last_error", "gcp_init_guess", "gcp_step", "gcp_solve", "gcp_get_history",
-           "gcp_solve_batched", "gcp_backward", "gcp_time_kernels")
+           "gcp_solve_batched", "gcp_backward", "gcp_time_kernels", "gcp_solve_noalloc")
 
 
 class Options(C.Structure):
@@ -85,8 +85,11 @@ def load_library(path: str = LIB_PATH):
                                           C.POINTER(Result), C.POINTER(Options)]
         lib.gcp_backward.argtypes = [vp, vp, ip, ip, ip, ip, vp, dp, vp, C.POINTER(Options)]
         lib.gcp_time_kernels.argtypes = [vp, ip, ip, ip, ip, C.POINTER(dp), C.POINTER(Options)]
+        lib.gcp_solve_noalloc.argtypes = [vp, ip, ip, ip, ip, vp, ip, ip, C.POINTER(Result),
+                                          C.POINTER(Options), C.c_char_p, ip]
         for name in ("gcp_create", "gcp_destroy", "gcp_init_guess", "gcp_step", "gcp_solve",
-                     "gcp_get_history", "gcp_solve_batched", "gcp_backward", "gcp_time_kernels"):
+                     "gcp_get_history", "gcp_solve_batched", "gcp_backward", "gcp_time_kernels",
+                     "gcp_solve_noalloc"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
