@@ -24,7 +24,7 @@ using namespace gcp;
 
 namespace {
 
-constexpr float kSplitScale = 1024.0f;
+constexpr float kSplitScale = 16384.0f;  // 2^14: see Split in gcp_device.cuh
 constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
 
 struct Handle {

@@ -47,27 +47,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-// Split a value of the shifted state into two 16-bit halves.
-//   fp16: h = rn(v), l = rn((v - h) * 2^11)   -> v ~ h + 2^-11 l
-//   bf16: h = rn(v), l = rn(v - h)            -> v ~ h + l
-// v is the FP32 value already multiplied by the global split scale.
+// Split a value of the shifted state into two 16-bit halves,
+//   h = rn(v), l = rn(v - h),  v ~ h + l,
+// where v is the FP32 value already multiplied by the global split scale
+// (2^14).  Both halves are stored at their true weight so that all three
+// products accumulate into one accumulator.  For fp16 the scale keeps
+// every |v| >= 2^-3 in the normal range of the remainder l (fp16 normals
+// start at 2^-14), so l carries 11 bits; smaller elements keep an absolute
+// error below 2^-25 / 2^14.  |X| <= 1.5 keeps |v| below the fp16 maximum.
 template <bool BF16>
 struct Split;
 
 template <>
 struct Split<false> {
   using T = __half;
-  static constexpr float kLoWeight = 1.0f / 2048.0f;
   __device__ __forceinline__ static void split(float v, T& h, T& l) {
     h = __float2half_rn(v);
-    l = __float2half_rn((v - __half2float(h)) * 2048.0f);
+    l = __float2half_rn(v - __half2float(h));
   }
 };
 
 template <>
 struct Split<true> {
   using T = __nv_bfloat16;
-  static constexpr float kLoWeight = 1.0f;
   __device__ __forceinline__ static void split(float v, T& h, T& l) {
     h = __float2bfloat16_rn(v);
     l = __float2bfloat16_rn(v - __bfloat162float(h));
