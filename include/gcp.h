@@ -148,10 +148,15 @@ gcp_status gcp_solve(void* handle, const void* H, int M, int N, int ld, int h_dt
  * GCP_HISTORY_FIELDS doubles); *n_out = records written. */
 gcp_status gcp_get_history(void* handle, double* out, int cap, int* n_out);
 
-/* Many independent solves of uneven size in one call.  H[b], D_out[b]:
- * device pointers; M[b], N[b], ld[b]: host arrays of length batch; all H in
- * h_dtype and all D in d_dtype.  res: host array of `batch` results (may be
- * NULL).  Instances converge independently (per-instance c_n and stop). */
+/* Many independent solves of uneven size in one call (the same recursion and
+ * readings as gcp_solve, applied to each instance).  H[b], D_out[b]: device
+ * pointers (host arrays of `batch` pointers); H[b] is M[b] x M[b] with
+ * leading dimension ld[b], D_out[b] is dense M[b] x M[b] (leading dimension
+ * M[b]); M, N, ld: host arrays of length batch; all H in h_dtype and all D in
+ * d_dtype.  res: host array of `batch` results (may be NULL).  Every kernel
+ * of a step is one launch over the tiles of all instances; each instance has
+ * its own c_n, stop test and status, and a stopped instance adds no work.
+ * history_cap must be 0.  Returns the first non-OK instance status. */
 gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, const int* M,
                              const int* N, const int* ld, int h_dtype, void* const* D_out,
                              int d_dtype, gcp_result* res, const gcp_options* opt);

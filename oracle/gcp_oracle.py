@@ -39,9 +39,12 @@ specification, not by code):
    trace for any value of c (Eqs. mcwgamb, hpcp1a).
 2. Two stop tests are offered: ||D^2 - D||_F <= tol (computed elementwise)
    and Tr(D Dbar) <= tol (the paper's test).
-3. 0/0 guard: stop when den = Tr(D - D^2) <= den_min with
-   den_min = 16 * M * u * max(1, Tr D) (u = 2^-53).  An initial c outside
-   [0, 1] is reported as ill-conditioned (Eqs. pmcpcons1-3 violated).
+3. 0/0 guard: when den = Tr(D - D^2) <= den_min with
+   den_min = 16 * M * u * max(1, Tr D) (u = 2^-53) and the stop test still
+   fails, the step uses c = 1/2 (the McWeeny step of Eq. mcweeny3, which the
+   recursion reaches as gamma -> 0): c itself would be rounding noise over
+   rounding noise.  An initial c outside [0, 1] is reported as
+   ill-conditioned (Eqs. pmcpcons1-3 violated).
 4. Stagnation: once R < 1e-8, two consecutive non-decreasing R stop the
    loop (converged if R <= tol).
 5. H = mu*I (Gershgorin interval of width <= 8 M u max(1, max|H_ii|)):
@@ -244,13 +247,16 @@ def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None
                 break
         den_min = 16.0 * M * U_FP64 * max(1.0, T1)
         if den <= den_min:
-            hist.append(rec)
             if fixed_iters > 0:
+                hist.append(rec)
                 n += 1
                 continue  # identity step
-            status = STATUS_OK if R <= tol else STATUS_NOT_CONVERGED
-            break
-        c = (T2 - T3) / den
+            # Tr(D Dbar) is at rounding level but R > tol: c would be noise
+            # over noise, so take the McWeeny step (c = 1/2, gamma = 0), the
+            # regime the recursion itself ends in (Eq. mcweeny3)
+            c = 0.5
+        else:
+            c = (T2 - T3) / den
         rec["c"] = c
         hist.append(rec)
         if n == 0 and not (0.0 <= c <= 1.0) and fixed_iters == 0:

@@ -59,6 +59,13 @@ struct Handle {
   std::vector<char> key;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // batched solves: one arena for every instance's buffers, the instance
+  // table, the work lists and a cached graph
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  std::vector<char> bkey;
+  cudaGraph_t bgraph = nullptr;
+  cudaGraphExec_t bexec = nullptr;
 };
 
 gcp_status fail(Handle* h, gcp_status s, const char* fmt, ...) {
@@ -413,6 +420,9 @@ gcp_status gcp_destroy(void* hv) {
   Handle* h = (Handle*)hv;
   if (!h) return GCP_ERR_INVALID_ARG;
   drop_graph(h);
+  if (h->bexec) cudaGraphExecDestroy(h->bexec);
+  if (h->bgraph) cudaGraphDestroy(h->bgraph);
+  cudaFree(h->arena);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->D64[i]);
     cudaFree(h->X[i]);
@@ -641,17 +651,321 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
                              gcp_result* res, const gcp_options* opt) {
   Handle* h = (Handle*)hv;
   if (!h) return GCP_ERR_INVALID_ARG;
-  (void)batch;
-  (void)H;
-  (void)M;
-  (void)N;
-  (void)ld;
-  (void)h_dtype;
-  (void)D_out;
-  (void)d_dtype;
-  (void)res;
-  (void)opt;
-  return fail(h, GCP_ERR_UNSUPPORTED, "gcp_solve_batched: not built yet");
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  if (batch <= 0 || !H || !M || !N || !ld || !D_out || !valid_dtype(h_dtype) ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
+      !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || o.history_cap != 0)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad arguments");
+  for (int b = 0; b < batch; ++b)
+    if (!H[b] || !D_out[b] || M[b] <= 0 || N[b] < 0 || N[b] > M[b] || ld[b] < M[b])
+      return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad instance %d", b);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const bool split = is_split(o.prec), mixed = is_mixed(o.prec);
+  const int bf16 = split_bf16(o.prec);
+  const int h64 = h_dtype == GCP_F64, d64 = d_dtype == GCP_F64;
+  if (res) memset(res, 0, sizeof(gcp_result) * (size_t)batch);
+
+  // trivial fillings: D = 0 or D = I, one instance at a time
+  std::vector<int> idx;
+  gcp_status r = ensure_common(h, 1, 1024, 0);
+  if (r != GCP_OK) return r;
+  for (int b = 0; b < batch; ++b) {
+    if (N[b] == 0 || N[b] == M[b]) {
+      if ((r = ensure_common(h, 1, M[b], 0)) != GCP_OK) return r;
+      launch_fill(nullptr, D_out[b], d64, M[b], M[b], N[b] == 0 ? 0.0 : 1.0, s);
+      launch_energy(D_out[b], d64, M[b], H[b], h64, ld[b], M[b], h->gpart, h->st, s);
+      State hs;
+      CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (res) {
+        res[b].status = GCP_OK;
+        res[b].trace = N[b];
+        res[b].energy = hs.E;
+      }
+    } else {
+      idx.push_back(b);
+    }
+  }
+  const int nb = (int)idx.size();
+  if (nb == 0) return GCP_OK;
+
+  // ---- layout of the arena -------------------------------------------
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  std::vector<BatchItem> items(nb);
+  std::vector<size_t> inst_off(nb);
+  size_t off = al(sizeof(State) * (size_t)nb);  // states first, contiguous
+  int ntc = 0, nf64 = 0, maxM = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int b = idx[k];
+    BatchItem& it = items[k];
+    memset(&it, 0, sizeof it);
+    it.M = M[b];
+    it.Mp = tc_pad(M[b]);
+    it.N = N[b];
+    it.ld = ld[b];
+    it.ldd = M[b];
+    it.H = H[b];
+    it.D_out = D_out[b];
+    it.gblocks = guess_partial_blocks(M[b]);
+    maxM = M[b] > maxM ? M[b] : maxM;
+    inst_off[k] = off;
+    if (split) {
+      const size_t n2 = (size_t)it.Mp * it.Mp;
+      off += al(tc_map_bytes());
+      off += 3 * al(n2 * 4) + 6 * al(n2 * 2);
+      it.tc_off = ntc;
+      it.tc_n = tc_num_tiles(it.Mp);
+      ntc += it.tc_n;
+    }
+    if (!split || mixed) {
+      off += 3 * al((size_t)it.M * it.M * 8);
+      it.f64_off = nf64;
+      it.f64_n = batch_f64_tiles(it.M);
+      nf64 += it.f64_n;
+    }
+  }
+  const size_t items_off = off;
+  off += al(sizeof(BatchItem) * (size_t)nb);
+  const size_t tinst_tc_off = off;
+  off += al(sizeof(int) * (size_t)(ntc > 0 ? ntc : 1));
+  const size_t tinst_f64_off = off;
+  off += al(sizeof(int) * (size_t)(nf64 > 0 ? nf64 : 1));
+  const size_t part_off = off;
+  off += al(sizeof(double) * kPartFields * (size_t)(ntc > nf64 ? ntc : nf64));
+  const size_t gpart_off = off;
+  const int gstride = guess_partial_blocks(maxM);
+  off += al(sizeof(double) * 4 * (size_t)gstride * (size_t)nb);
+  const size_t active_off = off;
+  off += al(sizeof(int));
+  if (off > h->arena_bytes) {
+    if (h->bexec) cudaGraphExecDestroy(h->bexec);
+    if (h->bgraph) cudaGraphDestroy(h->bgraph);
+    h->bexec = nullptr;
+    h->bgraph = nullptr;
+    h->bkey.clear();
+    cudaFree(h->arena);
+    h->arena = nullptr;
+    h->arena_bytes = 0;
+    CK(cudaMalloc((void**)&h->arena, off));
+    h->arena_bytes = off;
+  }
+  char* A = h->arena;
+  State* states = (State*)A;
+  BatchItem* items_d = (BatchItem*)(A + items_off);
+  int* tinst_tc = (int*)(A + tinst_tc_off);
+  int* tinst_f64 = (int*)(A + tinst_f64_off);
+  double* part = (double*)(A + part_off);
+  double* gpart = (double*)(A + gpart_off);
+  int* active = (int*)(A + active_off);
+
+  // key: everything the recorded graph depends on
+  std::vector<char> key;
+  auto put = [&key](const void* p, size_t n) {
+    key.insert(key.end(), (const char*)p, (const char*)p + n);
+  };
+  {
+    gcp_options k = o;
+    k.stream = nullptr;
+    put(&k, sizeof k);
+    put(&batch, sizeof batch);
+    put(&h_dtype, sizeof h_dtype);
+    put(&d_dtype, sizeof d_dtype);
+    put(H, sizeof(void*) * batch);
+    put(D_out, sizeof(void*) * batch);
+    put(M, sizeof(int) * batch);
+    put(N, sizeof(int) * batch);
+    put(ld, sizeof(int) * batch);
+    put(&h->arena, sizeof h->arena);
+  }
+  const bool fresh = !(o.use_graph && h->bexec && key == h->bkey);
+  if (fresh) {
+    // fill the instance table, tensor maps and work lists
+    std::vector<char> maps_host(tc_map_bytes());
+    std::vector<int> tt(ntc > 0 ? ntc : 1), tf(nf64 > 0 ? nf64 : 1);
+    char errbuf[256] = {0};
+    for (int k = 0; k < nb; ++k) {
+      BatchItem& it = items[k];
+      it.st = &states[k];
+      char* p = A + inst_off[k];
+      if (split) {
+        const size_t n2 = (size_t)it.Mp * it.Mp;
+        char* maps_dev = p;
+        p += al(tc_map_bytes());
+        it.X[0] = (float*)p;
+        p += al(n2 * 4);
+        it.X[1] = (float*)p;
+        p += al(n2 * 4);
+        it.Sig = (float*)p;
+        p += al(n2 * 4);
+        it.Xh[0] = p;
+        p += al(n2 * 2);
+        it.Xl[0] = p;
+        p += al(n2 * 2);
+        it.Xh[1] = p;
+        p += al(n2 * 2);
+        it.Xl[1] = p;
+        p += al(n2 * 2);
+        it.Sh = p;
+        p += al(n2 * 2);
+        it.Sl = p;
+        p += al(n2 * 2);
+        if (tc_build_batch_maps(maps_host.data(), it, bf16, errbuf, sizeof errbuf))
+          return fail(h, GCP_ERR_CUDA, "gcp_solve_batched: %s", errbuf);
+        CK(cudaMemcpy(maps_dev, maps_host.data(), tc_map_bytes(), cudaMemcpyHostToDevice));
+        it.maps = maps_dev;
+        for (int t = 0; t < it.tc_n; ++t) tt[it.tc_off + t] = k;
+      }
+      if (!split || mixed) {
+        const size_t m2 = (size_t)it.M * it.M;
+        for (int i = 0; i < 2; ++i) {
+          it.D64[i] = (double*)p;
+          p += al(m2 * 8);
+        }
+        it.S64 = (double*)p;
+        p += al(m2 * 8);
+        for (int t = 0; t < it.f64_n; ++t) tf[it.f64_off + t] = k;
+      }
+    }
+    CK(cudaMemcpy(items_d, items.data(), sizeof(BatchItem) * nb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tinst_tc, tt.data(), sizeof(int) * tt.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tinst_f64, tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice));
+  }
+
+  Ctl c1{}, c0{};
+  c1.stop = c0.stop = o.stop;
+  c1.max_iter = c0.max_iter = o.max_iter;
+  c1.fixed_iters = c0.fixed_iters = o.fixed_iters;
+  c1.tol = c0.tol = o.tol;
+  c1.phase = 1;
+  c1.final_phase = mixed ? 0 : 1;
+  c1.endgame = 1;
+  c1.u = kU32;
+  c0.phase = 0;
+  c0.final_phase = 1;
+  c0.endgame = split ? 1 : 0;
+  c0.u = kU64;
+
+  auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
+    if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, ss))
+      return fail(h, GCP_ERR_CUDA, "batched GEMM1 launch failed");
+    launch_batch_control(part, items_d, nb, c1, ss);
+    if (tc_launch_batch_gemm(2, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, ss))
+      return fail(h, GCP_ERR_CUDA, "batched GEMM2 launch failed");
+    launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
+    CK(cudaPeekAtLastError());
+    return GCP_OK;
+  };
+  auto f64_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
+    launch_batch_f64_gemm1(items_d, nb, tinst_f64, nf64, part, ss);
+    launch_batch_control(part, items_d, nb, c0, ss);
+    launch_batch_f64_gemm2(items_d, nb, tinst_f64, nf64, ss);
+    launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
+    CK(cudaPeekAtLastError());
+    return GCP_OK;
+  };
+  // one phase: a WHILE node when capturing, else a host loop on the flag
+  auto run_phase = [&](auto& body, cudaStream_t ss, bool graph) -> gcp_status {
+    if (graph) {
+      cudaStreamCaptureStatus cst;
+      unsigned long long id = 0;
+      cudaGraph_t g = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* edata = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(ss, &cst, &id, &g, &deps, &edata, &nd));
+      cudaGraphConditionalHandle cond;
+      CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+      p.conditional.handle = cond;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, g, deps, edata, nd, &p));
+      cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+      CK(cudaStreamUpdateCaptureDependencies(ss, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies));
+      CK(cudaStreamBeginCaptureToGraph(h->body, bodyg, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeRelaxed));
+      gcp_status rr = body(cond, h->body, 1);
+      cudaGraph_t outg = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->body, &outg);
+      if (rr != GCP_OK) return rr;
+      if (e != cudaSuccess) return fail(h, GCP_ERR_CUDA, "body capture: %s", cudaGetErrorString(e));
+      return GCP_OK;
+    }
+    const int cap = (o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
+    for (int it = 0; it < cap; ++it) {
+      gcp_status rr = body(0, ss, 0);
+      if (rr != GCP_OK) return rr;
+      int hostact = 0;
+      CK(cudaMemcpyAsync(&hostact, active, sizeof hostact, cudaMemcpyDeviceToHost, ss));
+      CK(cudaStreamSynchronize(ss));
+      if (!hostact) break;
+    }
+    return GCP_OK;
+  };
+  auto record = [&](cudaStream_t ss, bool graph) -> gcp_status {
+    launch_batch_guess(items_d, nb, maxM, h64, split ? 1 : 0, bf16, kSplitScale, gpart, gstride,
+                       ss);
+    launch_batch_state_init(items_d, nb, split ? 1 : 0, ss);
+    CK(cudaPeekAtLastError());
+    gcp_status rr;
+    if (split && (rr = run_phase(split_body, ss, graph)) != GCP_OK) return rr;
+    if (mixed) {
+      launch_batch_x_to_d64(items_d, nb, maxM, ss);
+      launch_batch_phase_begin(items_d, nb, 0, ss);
+    }
+    if ((!split || mixed) && (rr = run_phase(f64_body, ss, graph)) != GCP_OK) return rr;
+    launch_batch_copy_out(items_d, nb, maxM, split && !mixed ? 1 : 0, d64, ss);
+    launch_batch_energy(items_d, nb, d64, h64, gpart, gstride, ss);
+    CK(cudaPeekAtLastError());
+    return GCP_OK;
+  };
+  if (o.use_graph) {
+    if (fresh) {
+      if (h->bexec) cudaGraphExecDestroy(h->bexec);
+      if (h->bgraph) cudaGraphDestroy(h->bgraph);
+      h->bexec = nullptr;
+      h->bgraph = nullptr;
+      h->bkey.clear();
+      CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
+      r = record(h->cap, true);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+      if (r != GCP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess)
+        return fail(h, GCP_ERR_CUDA, "batched capture: %s", cudaGetErrorString(e));
+      h->bgraph = g;
+      CK(cudaGraphInstantiate(&h->bexec, g, 0));
+      h->bkey = key;
+    }
+    CK(cudaGraphLaunch(h->bexec, s));
+  } else {
+    if ((r = record(s, false)) != GCP_OK) return r;
+  }
+  std::vector<State> hs(nb);
+  CK(cudaMemcpyAsync(hs.data(), states, sizeof(State) * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  gcp_status worst = GCP_OK;
+  for (int k = 0; k < nb; ++k) {
+    if (hs[k].timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");
+    if (res) {
+      fill_result(hs[k], &res[idx[k]]);
+      res[idx[k]].energy = hs[k].E;
+    }
+    if (hs[k].status != GCP_OK && worst == GCP_OK) worst = (gcp_status)hs[k].status;
+  }
+  if (worst != GCP_OK)
+    return fail(h, worst, "gcp_solve_batched: an instance ended with: %s",
+                gcp_status_string(worst));
+  return GCP_OK;
 }
 
 gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dtype,

@@ -21,24 +21,10 @@ namespace gcp {
 namespace {
 constexpr int kCtlThreads = 256;
 
-__global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __restrict__ part,
-                                                              int ntiles, State* st, double* hist,
-                                                              Ctl ctl,
-                                                              cudaGraphConditionalHandle cond,
-                                                              int use_cond) {
-  __shared__ double red[32 * 5];
-  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    const double* p = part + (size_t)t * kPartFields;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) v[k] += p[k];
-  }
-  block_sum<5>(v, red);
-  if (threadIdx.x != 0) return;
-  if (st->stopped) {
-    if (use_cond) cudaGraphSetConditional(cond, 0);
-    return;
-  }
+// One control decision from the summed partials v of the iterate's GEMM1.
+// Returns 1 when the phase stops for this state (already stopped included).
+__device__ int control_decide(const double (&v)[5], State* st, double* hist, const Ctl& ctl) {
+  if (st->stopped) return 1;
   // FP64 phase: v = (Tr D, Tr S, sum S o D, R^2, E).
   // Split phase, on D = theta J + X and S = theta^2 J + Sigma (J the identity
   // on the unpadded block): v = (Tr X, Tr Sigma, sum Sigma o X, R^2, E) and
@@ -144,9 +130,20 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
         stop = 1;
         kind = 2;
       } else {
-        stop = 1;
-        kind = 3;
-        status = GCP_ERR_NOT_CONVERGED;
+        // FP64, Tr(D - D^2) at rounding level but R > tol: McWeeny step
+        // (c = 1/2), as in the oracle; the stagnation rule ends a loop that
+        // can go no further
+        st->c = 0.5;
+        st->a = 0.0;
+        st->b = 3.0;
+        const double th = st->theta;
+        st->xshift = 2.0 * th * (1.0 - th) * (th - 0.5);
+        st->apply = 1;
+        st->Rp1 = st->Rp0;
+        st->Rp0 = R;
+        st->n = n + 1;
+        st->parity ^= 1;
+        if (rec) rec[5] = 0.5;
       }
     } else {
       // Split phase (before the endgame): c also absorbs the FP32 rounding
@@ -207,10 +204,81 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
       }
     }
   }
+  return stop;
+}
+
+__global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __restrict__ part,
+                                                              int ntiles, State* st, double* hist,
+                                                              Ctl ctl,
+                                                              cudaGraphConditionalHandle cond,
+                                                              int use_cond) {
+  __shared__ double red[32 * 5];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const double* p = part + (size_t)t * kPartFields;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] += p[k];
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  const int stop = control_decide(v, st, hist, ctl);
   if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
-__global__ void state_init_kernel(State* st, int phase) {
+// Batched control: block b decides for instance b from its own tiles'
+// partial sums (per-instance c_n and stop mask).
+__global__ void __launch_bounds__(kCtlThreads) batch_control_kernel(const double* __restrict__ part,
+                                                                    const BatchItem* items,
+                                                                    Ctl ctl) {
+  __shared__ double red[32 * 5];
+  const BatchItem& it = items[blockIdx.x];
+  const int off = ctl.phase == 1 ? it.tc_off : it.f64_off;
+  const int n = ctl.phase == 1 ? it.tc_n : it.f64_n;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const double* p = part + (size_t)(off + t) * kPartFields;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] += p[k];
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  Ctl c = ctl;
+  c.M = it.M;
+  c.N = it.N;
+  control_decide(v, it.st, nullptr, c);
+}
+
+// WHILE condition of a batched phase: continue while any instance runs.
+__global__ void batch_any_active_kernel(const BatchItem* items, int batch,
+                                        cudaGraphConditionalHandle cond, int use_cond,
+                                        int* active_out) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < batch; b += blockDim.x)
+    if (!items[b].st->stopped) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (active_out) *active_out = any;
+    if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+__device__ void state_init_dev(State* st, int phase);
+__device__ void phase_begin_dev(State* st, int phase);
+
+__global__ void state_init_kernel(State* st, int phase) { state_init_dev(st, phase); }
+__global__ void phase_begin_kernel(State* st, int phase) { phase_begin_dev(st, phase); }
+__global__ void batch_state_init_kernel(const BatchItem* items, int batch, int phase) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) state_init_dev(items[b].st, phase);
+}
+__global__ void batch_phase_begin_kernel(const BatchItem* items, int batch, int phase) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) phase_begin_dev(items[b].st, phase);
+}
+
+__device__ void state_init_dev(State* st, int phase) {
   // zero everything except the guess parameters written just before
   st->n = 0;
   st->n_lowp = 0;
@@ -236,7 +304,7 @@ __global__ void state_init_kernel(State* st, int phase) {
   st->xshift = 0.0;
 }
 
-__global__ void phase_begin_kernel(State* st, int phase) {
+__device__ void phase_begin_dev(State* st, int phase) {
   // the FP64 refinement runs only after a split phase that reached its floor
   const int go = st->lowp_done && !st->converged && !st->terminal && !st->no_gap;
   st->stopped = go ? 0 : 1;
@@ -451,5 +519,119 @@ void launch_energy(const void* D, int d_f64, int ldd, const void* H, int h_f64, 
     energy_kernel<float, float><<<nb, 256, 0, s>>>((const float*)D, ldd, (const float*)H, ldh, M,
                                                   part);
   energy_finalize_kernel<<<1, 32, 0, s>>>(part, nb, st);
+}
+
+// ---- batched elementwise kernels (grid.z / grid.y = instance) ------------
+namespace {
+__global__ void batch_x_to_d64_kernel(const BatchItem* items) {
+  const BatchItem& it = items[blockIdx.z];
+  const int i = blockIdx.y;
+  if (i >= it.M) return;
+  const float* src = it.st->parity ? it.X[1] : it.X[0];
+  const double th = it.st->theta;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x) {
+    double v = (double)src[(size_t)(i < j ? i : j) * it.Mp + (i < j ? j : i)];
+    if (i == j) v += th;
+    it.D64[0][(size_t)i * it.M + j] = v;
+  }
+}
+
+template <typename O>
+__global__ void batch_copy_out_kernel(const BatchItem* items, int from_x) {
+  const BatchItem& it = items[blockIdx.z];
+  const int i = blockIdx.y;
+  if (i >= it.M) return;
+  O* out = (O*)it.D_out;
+  const int p = it.st->parity;
+  if (from_x) {
+    const float* src = it.X[p];
+    const double th = it.st->theta;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x) {
+      double v = (double)src[(size_t)i * it.Mp + j];
+      if (i == j) v += th;
+      out[(size_t)i * it.ldd + j] = (O)v;
+    }
+  } else {
+    const double* src = it.D64[p];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x)
+      out[(size_t)i * it.ldd + j] = (O)src[(size_t)i * it.M + j];
+  }
+}
+
+template <typename DT, typename HT>
+__global__ void __launch_bounds__(256) batch_energy_kernel(const BatchItem* items,
+                                                           double* __restrict__ part) {
+  __shared__ double red[32];
+  const BatchItem& it = items[blockIdx.y];
+  if ((int)blockIdx.x >= it.gblocks) return;  // the single-solve block layout
+  const DT* D = (const DT*)it.D_out;
+  const HT* H = (const HT*)it.H;
+  double v[1] = {0.0};
+  const int warps = blockDim.x / 32;
+  const int gw = blockIdx.x * warps + (threadIdx.x >> 5), nw = it.gblocks * warps;
+  const int lane = threadIdx.x & 31;
+  for (int i = gw; i < it.M; i += nw) {
+    for (int j = lane; j < it.M; j += 32)
+      v[0] += (double)D[(size_t)i * it.ldd + j] * (double)H[(size_t)i * it.ld + j];
+  }
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+}
+
+__global__ void batch_energy_finalize_kernel(const BatchItem* items, int batch,
+                                             const double* __restrict__ part, int gstride) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double e = 0.0;
+  for (int k = 0; k < items[b].gblocks; ++k) e += part[(size_t)b * gstride + k];
+  items[b].st->E = e;
+}
+}  // namespace
+
+void launch_batch_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
+                          cudaStream_t s) {
+  batch_control_kernel<<<batch, kCtlThreads, 0, s>>>(part, items, ctl);
+}
+
+void launch_batch_any_active(const BatchItem* items, int batch, unsigned long long cond,
+                             int use_cond, int* active_out, cudaStream_t s) {
+  batch_any_active_kernel<<<1, 256, 0, s>>>(items, batch, (cudaGraphConditionalHandle)cond,
+                                            use_cond, active_out);
+}
+
+void launch_batch_state_init(const BatchItem* items, int batch, int phase, cudaStream_t s) {
+  batch_state_init_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, phase);
+}
+
+void launch_batch_phase_begin(const BatchItem* items, int batch, int phase, cudaStream_t s) {
+  batch_phase_begin_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, phase);
+}
+
+void launch_batch_x_to_d64(const BatchItem* items, int batch, int maxM, cudaStream_t s) {
+  dim3 g((maxM + 255) / 256 < 4 ? (maxM + 255) / 256 : 4, maxM, batch);
+  batch_x_to_d64_kernel<<<g, 256, 0, s>>>(items);
+}
+
+void launch_batch_copy_out(const BatchItem* items, int batch, int maxM, int from_x, int out_f64,
+                           cudaStream_t s) {
+  dim3 g((maxM + 255) / 256 < 4 ? (maxM + 255) / 256 : 4, maxM, batch);
+  if (out_f64)
+    batch_copy_out_kernel<double><<<g, 256, 0, s>>>(items, from_x);
+  else
+    batch_copy_out_kernel<float><<<g, 256, 0, s>>>(items, from_x);
+}
+
+void launch_batch_energy(const BatchItem* items, int batch, int out_f64, int h_f64, double* gpart,
+                         int gstride, cudaStream_t s) {
+  dim3 g(gstride, batch);
+  if (out_f64 && h_f64)
+    batch_energy_kernel<double, double><<<g, 256, 0, s>>>(items, gpart);
+  else if (out_f64)
+    batch_energy_kernel<double, float><<<g, 256, 0, s>>>(items, gpart);
+  else if (h_f64)
+    batch_energy_kernel<float, double><<<g, 256, 0, s>>>(items, gpart);
+  else
+    batch_energy_kernel<float, float><<<g, 256, 0, s>>>(items, gpart);
+  batch_energy_finalize_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, gpart, gstride);
 }
 }  // namespace gcp

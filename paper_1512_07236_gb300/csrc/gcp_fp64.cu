@@ -205,4 +205,121 @@ void launch_f64_gemm2(const double* S, const double* D, double* Dn, int M, int l
     f64_gemm2_kernel<64><<<nt, kThreads, 0, s>>>(S, D, Dn, M, ld, st);
 }
 
+// ---- batched: one launch over the tiles of every instance ----------------
+// tile_inst[t] names the instance of work-list tile t; the instance's tiles
+// are the 32 x 32 upper tiles of its matrix, in the order of tile_coords.
+namespace {
+constexpr int kBT = 32;
+
+__global__ void __launch_bounds__(kThreads) batch_f64_gemm1_kernel(const BatchItem* items,
+                                                                   const int* tile_inst,
+                                                                   double* __restrict__ part) {
+  const BatchItem& it = items[tile_inst[blockIdx.x]];
+  State* st = it.st;
+  if (st->stopped) return;
+  __shared__ double As[kBK][kBT];
+  __shared__ double Bs[kBK][kBT];
+  __shared__ double red[32 * 5];
+  constexpr int RT = kBT / 16;
+  const int M = it.M, ld = it.M;
+  const double* D = it.D64[st->parity];
+  double* S = it.S64;
+  const int T = (M + kBT - 1) / kBT;
+  int bi, bj;
+  tile_coords(blockIdx.x - it.f64_off, T, bi, bj);
+  const int m0 = bi * kBT, n0 = bj * kBT;
+  double acc[RT][RT];
+  f64_mainloop<kBT>(D, D, M, ld, m0, n0, acc, As, Bs);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    const int r = m0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (r < M && c < M && c >= r) {
+        const double w = (c == r) ? 1.0 : 2.0;
+        const double s = acc[i][j];
+        const double d = D[(size_t)r * ld + c];
+        if (r == c) {
+          v[0] += d;
+          v[1] += s;
+        }
+        v[2] += w * s * d;
+        v[3] += w * (s - d) * (s - d);
+        S[(size_t)r * ld + c] = s;
+        if (c != r) S[(size_t)c * ld + r] = s;
+      }
+    }
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    double* p = part + (size_t)blockIdx.x * kPartFields;
+    p[0] = v[0];
+    p[1] = v[1];
+    p[2] = v[2];
+    p[3] = v[3];
+    p[4] = 0.0;
+    p[5] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_f64_gemm2_kernel(const BatchItem* items,
+                                                                   const int* tile_inst) {
+  const BatchItem& it = items[tile_inst[blockIdx.x]];
+  const State* st = it.st;
+  if (st->stopped) return;
+  __shared__ double As[kBK][kBT];
+  __shared__ double Bs[kBK][kBT];
+  constexpr int RT = kBT / 16;
+  const int M = it.M, ld = it.M;
+  // the control kernel has flipped the parity for this step
+  const double* D = it.D64[st->parity ^ 1];
+  double* Dn = it.D64[st->parity];
+  const double* S = it.S64;
+  const int T = (M + kBT - 1) / kBT;
+  int bi, bj;
+  tile_coords(blockIdx.x - it.f64_off, T, bi, bj);
+  const int m0 = bi * kBT, n0 = bj * kBT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool apply = st->apply != 0;
+  const double a = st->a, b = st->b;
+  double acc[RT][RT];
+  if (apply) f64_mainloop<kBT>(S, D, M, ld, m0, n0, acc, As, Bs);
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    const int r = m0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+      const int c = n0 + tx + 16 * j;
+      if (r < M && c < M && c >= r) {
+        const size_t o = (size_t)r * ld + c;
+        const double d = D[o];
+        const double x = apply ? (a * d + b * S[o] - 2.0 * acc[i][j]) : d;
+        Dn[o] = x;
+        if (c != r) Dn[(size_t)c * ld + r] = x;
+      }
+    }
+  }
+}
+}  // namespace
+
+int batch_f64_tiles(int M) {
+  const int T = (M + kBT - 1) / kBT;
+  return T * (T + 1) / 2;
+}
+
+void launch_batch_f64_gemm1(const BatchItem* items, int batch, const int* tile_inst, int ntiles,
+                            double* part, cudaStream_t s) {
+  (void)batch;
+  batch_f64_gemm1_kernel<<<ntiles, kThreads, 0, s>>>(items, tile_inst, part);
+}
+
+void launch_batch_f64_gemm2(const BatchItem* items, int batch, const int* tile_inst, int ntiles,
+                            cudaStream_t s) {
+  (void)batch;
+  batch_f64_gemm2_kernel<<<ntiles, kThreads, 0, s>>>(items, tile_inst);
+}
+
 }  // namespace gcp

@@ -50,6 +50,31 @@ struct Ctl {
 // Number of partial-sum fields written per GEMM1 tile.
 constexpr int kPartFields = 6;  // T1, T2, T3, R^2, E, spare
 
+// Per-instance descriptor of a batched solve (device memory).  Every
+// instance has its own state, buffers and slices of the batched work lists.
+// The iterate buffer in use is State::parity: GEMM1 reads buffer `parity`;
+// the control kernel flips it when it schedules an update, so GEMM2 reads
+// `parity ^ 1` and writes `parity`.
+struct BatchItem {
+  State* st;
+  const void* H;
+  void* D_out;
+  float* X[2];
+  void* Xh[2];
+  void* Xl[2];
+  float* Sig;
+  void* Sh;
+  void* Sl;
+  double* D64[2];
+  double* S64;
+  const void* maps;  // 6 tensor maps: X0 hi, X0 lo, X1 hi, X1 lo, Sigma hi, Sigma lo
+  int M, Mp, N, ld, ldd;
+  int tc_off, tc_n;    // tensor-core tiles in the batched work list
+  int f64_off, f64_n;  // FP64 tiles in the batched work list
+  int gblocks;         // reduction blocks of the guess/energy passes
+                       // (guess_partial_blocks(M): the single-solve layout)
+};
+
 // ---- guess (gcp_guess.cu) ------------------------------------------------
 int guess_partial_blocks(int M);
 // Gershgorin row bounds, trace, max|H_ii|: per-block partials (4 doubles).
@@ -116,5 +141,34 @@ int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X
                     float* Xn, void* Xnh, void* Xnl, int M, int Mp, State* st, int bf16,
                     float split_scale, int* dev_err, cudaStream_t s);
 void tc_set_smem_attrs();
+
+// ---- batched solves (many instances per launch) --------------------------
+// guess: per-instance Gershgorin/trace partials (gstride slots of 4 doubles
+// per instance in `gpart`, the instance using its own gblocks of them, in
+// the same order as a single solve), parameters into each State, then D0/X0.
+void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, int split,
+                        int bf16, float split_scale, double* gpart, int gstride, cudaStream_t s);
+void launch_batch_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
+                          cudaStream_t s);
+void launch_batch_any_active(const BatchItem* items, int batch, unsigned long long cond,
+                             int use_cond, int* active_out, cudaStream_t s);
+void launch_batch_state_init(const BatchItem* items, int batch, int phase, cudaStream_t s);
+void launch_batch_phase_begin(const BatchItem* items, int batch, int phase, cudaStream_t s);
+void launch_batch_x_to_d64(const BatchItem* items, int batch, int maxM, cudaStream_t s);
+void launch_batch_copy_out(const BatchItem* items, int batch, int maxM, int from_x, int out_f64,
+                           cudaStream_t s);
+void launch_batch_energy(const BatchItem* items, int batch, int out_f64, int h_f64, double* gpart,
+                         int gstride, cudaStream_t s);
+// FP64 products over the work list of all instances (32 x 32 tiles).
+int batch_f64_tiles(int M);
+void launch_batch_f64_gemm1(const BatchItem* items, int batch, const int* tile_inst, int ntiles,
+                            double* part, cudaStream_t s);
+void launch_batch_f64_gemm2(const BatchItem* items, int batch, const int* tile_inst, int ntiles,
+                            cudaStream_t s);
+// Tensor-core products over the work list of all instances.
+int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* err, int errlen);
+size_t tc_map_bytes();
+int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
+                         int ntiles, double* part, int bf16, float split_scale, cudaStream_t s);
 
 }  // namespace gcp

@@ -41,6 +41,7 @@
 // freeing its TMEM.
 #include <cuda.h>
 #include <stdio.h>
+#include <string.h>
 
 #include "gcp_device.cuh"
 #include "gcp_internal.cuh"
@@ -321,23 +322,84 @@ __device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base,
   }
 }
 
-template <int MODE, bool BF16>
+// Everything one tile needs: its block coordinates, operand maps, the
+// epilogue pointers of its instance and the update coefficients.
+struct TileCtx {
+  int I, J, nkb;
+  bool skip;  // instance stopped: no work at all
+  bool mma;   // products needed (false: identity copy of the iterate)
+  const CUtensorMap *ah, *al, *bh, *bl;
+  Epi ep;
+  float ca, cb, cj;
+};
+
+template <int MODE, bool BATCHED>
+__device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorMap* mAh,
+                                         const CUtensorMap* mAl, const CUtensorMap* mBh,
+                                         const CUtensorMap* mBl, const BatchItem* items,
+                                         const int* tile_inst, TileCtx& c) {
+  c.ep = base;
+  if (!BATCHED) {
+    tc_tile(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
+    c.skip = false;
+    c.ah = mAh;
+    c.al = mAl;
+    c.bh = mBh;
+    c.bl = mBl;
+  } else {
+    const BatchItem& it = items[tile_inst[t]];
+    State* st = it.st;
+    c.skip = st->stopped != 0;
+    const int par = st->parity;
+    const CUtensorMap* maps = (const CUtensorMap*)it.maps;
+    c.ep.st = st;
+    c.ep.M = it.M;
+    c.ep.Mp = it.Mp;
+    c.ep.H = nullptr;
+    if (MODE == 1) {
+      // GEMM1 reads the current buffer and writes Sigma
+      c.ep.X = it.X[par];
+      c.ep.out = it.Sig;
+      c.ep.out_h = it.Sh;
+      c.ep.out_l = it.Sl;
+      c.ah = c.bh = &maps[2 * par];
+      c.al = c.bl = &maps[2 * par + 1];
+    } else {
+      // the control kernel flipped the parity: read par^1, write par
+      c.ep.X = it.X[par ^ 1];
+      c.ep.Sig = it.Sig;
+      c.ep.out = it.X[par];
+      c.ep.out_h = it.Xh[par];
+      c.ep.out_l = it.Xl[par];
+      c.ah = &maps[2 * (par ^ 1)];
+      c.al = &maps[2 * (par ^ 1) + 1];
+      c.bh = &maps[4];
+      c.bl = &maps[5];
+    }
+    tc_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
+  }
+  const State* st = c.ep.st;
+  c.mma = !c.skip && (MODE == 1 || st->apply != 0);
+  c.nkb = c.mma ? c.ep.Mp / BK : 0;
+  c.ca = c.cb = c.cj = 0.f;
+  if (MODE == 2 && !c.skip) {
+    const double th = st->theta;
+    c.ca = (float)(st->a - 2.0 * th * th);
+    c.cb = (float)(st->b - 2.0 * th);
+    c.cj = (float)st->xshift;
+  }
+}
+
+template <int MODE, bool BF16, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                   const Epi ep) {
-  State* st = ep.st;
-  if (st->stopped || st->timeout) return;
-  const int NI = ep.Mp / BM, NJ = ep.Mp / BN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool do_mma = (MODE == 1) || st->apply;
-  float ca = 0.f, cb = 0.f, cj = 0.f;
-  if (MODE == 2) {
-    const double th = st->theta;
-    ca = (float)(st->a - 2.0 * th * th);
-    cb = (float)(st->b - 2.0 * th);
-    cj = (float)st->xshift;
+                   const Epi ep, const BatchItem* items, const int* tile_inst) {
+  if (!BATCHED) {
+    State* st = ep.st;
+    if (st->stopped || st->timeout) return;
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -349,25 +411,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
-
-  if (!do_mma) {
-    // identity step (fixed-iteration mode past the 0/0 guard): X_{n+1} = X
-    if (warp >= 2) {
-      // TMEM lane quarter is fixed by the warp's rank within its warpgroup
-      const int dw = warp - 2, q = warp & 3, half = dw >> 2;
-      float acc[128];
-      double dpart[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
-        int I, J;
-        tc_tile(t, NI, NJ, I, J);
-        const int jb = 2 * J + half;
-        if (jb < I) continue;
-        epilogue_row<MODE, BF16>(ep, I * BM + 32 * q + lane, J * BN + half * 128, jb == I, acc,
-                                 false, ca, cb, cj, dpart);
-      }
-    }
-    return;
-  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -391,8 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  const int nkb = ep.Mp / BK;                 // K blocks (stages) per tile
-  const int nchunk = nkb / KC_STAGES;         // TMEM drains per tile
+  int* timeout_flag = BATCHED ? &items[0].st->timeout : &ep.st->timeout;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -400,31 +442,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0;  // global stage counter
       bool alive = true;
       for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
-        int I, J;
-        tc_tile(t, NI, NJ, I, J);
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
+        TileCtx c;
+        make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
+        for (int kb = 0; kb < c.nkb; ++kb, ++g) {
           const uint32_t s = g % STAGES;
           if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1)) {
-            atomicOr(&st->timeout, 1);
+            atomicOr(timeout_flag, 1);
             alive = false;
             break;
           }
           const uint32_t stage = sbase + s * kStageBytes;
           mbar_expect_tx(&full_bar[s], kStageBytes);
           const int kx = kb * BK;
-          tma_load_2d(&mAh, &full_bar[s], stage, kx, I * BM);
-          tma_load_2d(&mAl, &full_bar[s], stage + kABytes, kx, I * BM);
-          tma_load_2d(&mBh, &full_bar[s], stage + 2 * kABytes, kx, J * BN);
-          tma_load_2d(&mBh, &full_bar[s], stage + 2 * kABytes + kBBytes / 2, kx, J * BN + 128);
-          tma_load_2d(&mBl, &full_bar[s], stage + 2 * kABytes + kBBytes, kx, J * BN);
-          tma_load_2d(&mBl, &full_bar[s], stage + 2 * kABytes + kBBytes + kBBytes / 2, kx,
-                      J * BN + 128);
+          tma_load_2d(c.ah, &full_bar[s], stage, kx, c.I * BM);
+          tma_load_2d(c.al, &full_bar[s], stage + kABytes, kx, c.I * BM);
+          tma_load_2d(c.bh, &full_bar[s], stage + 2 * kABytes, kx, c.J * BN);
+          tma_load_2d(c.bh, &full_bar[s], stage + 2 * kABytes + kBBytes / 2, kx, c.J * BN + 128);
+          tma_load_2d(c.bl, &full_bar[s], stage + 2 * kABytes + kBBytes, kx, c.J * BN);
+          tma_load_2d(c.bl, &full_bar[s], stage + 2 * kABytes + kBBytes + kBBytes / 2, kx,
+                      c.J * BN + 128);
         }
       }
       // every issued load must land before the CTA exits
       const uint32_t first = g > STAGES ? g - STAGES : 0;
       for (uint32_t k = first; k < g; ++k)
-        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(&st->timeout, 1);
+        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(timeout_flag, 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -433,10 +475,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0, qc = 0;  // global stage and chunk counters
       bool alive = true;
       for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
+        TileCtx c;
+        make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
+        const int nchunk = c.nkb / KC_STAGES;
         for (int ch = 0; ch < nchunk && alive; ++ch, ++qc) {
           const uint32_t b = qc & 1;
           if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
-            atomicOr(&st->timeout, 1);
+            atomicOr(timeout_flag, 1);
             alive = false;
             break;
           }
@@ -445,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ks = 0; ks < KC_STAGES; ++ks, ++g) {
             const uint32_t s = g % STAGES;
             if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
-              atomicOr(&st->timeout, 1);
+              atomicOr(timeout_flag, 1);
               alive = false;
               break;
             }
@@ -469,28 +514,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // every MMA issued here must be complete before TMEM is freed
       umma_commit(&fin_bar);
-      if (!mbar_wait(&fin_bar, 0)) atomicOr(&st->timeout, 1);
+      if (!mbar_wait(&fin_bar, 0)) atomicOr(timeout_flag, 1);
     }
   } else {
     // ---------------- drain + epilogue (warps 2..9) ----------------
     // TMEM lane quarter is fixed by the warp's rank within its warpgroup
-      const int dw = warp - 2, q = warp & 3, half = dw >> 2;
+    const int dw = warp - 2, q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     uint32_t qc = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
-      int I, J;
-      tc_tile(t, NI, NJ, I, J);
+      TileCtx c;
+      make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
+      if (c.skip) continue;  // uniform over the CTA
       float acc[128];
 #pragma unroll
       for (int k = 0; k < 128; ++k) acc[k] = 0.f;
+      const int nchunk = c.nkb / KC_STAGES;
       for (int ch = 0; ch < nchunk; ++ch, ++qc) {
         const uint32_t b = qc & 1;
         if (alive) {
           // warp-uniform: tcgen05.ld below is a warp-collective instruction
           const bool got = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1));
           if (!got) {
-            if (lane == 0) atomicOr(&st->timeout, 1);
+            if (lane == 0) atomicOr(timeout_flag, 1);
             alive = false;
           }
         }
@@ -511,12 +558,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // all drain warps agree on whether the tile completed
       drain_bar_sync();
-      const bool ok = alive && !(*(volatile int*)&st->timeout);
+      const bool ok = alive && !(*(volatile int*)timeout_flag);
       double dpart[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      const int jb = 2 * J + half;
-      if (ok && jb >= I)
-        epilogue_row<MODE, BF16>(ep, I * BM + 32 * q + lane, J * BN + half * 128, jb == I, acc,
-                                 true, ca, cb, cj, dpart);
+      const int jb = 2 * c.J + half;
+      if (ok && jb >= c.I)
+        epilogue_row<MODE, BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128,
+                                 jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, dpart);
       if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) dpart[k] = warp_sum(dpart[k]);
@@ -600,17 +647,26 @@ int sm_count() {
   return n;
 }
 
-template <int MODE, bool BF16>
-int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, cudaStream_t s) {
+template <int MODE, bool BF16, bool BATCHED>
+int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const BatchItem* items,
+              const int* tile_inst, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, BF16>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, BF16, BATCHED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return 1;
     attr = true;
   }
   const int grid = ep.ntiles < sm_count() ? ep.ntiles : sm_count();
-  tc_gemm_kernel<MODE, BF16><<<grid, kThreads, kSmemBytes, s>>>(A->hi, A->lo, B->hi, B->lo, ep);
+  if (BATCHED) {
+    CUtensorMap dummy;
+    memset(&dummy, 0, sizeof dummy);
+    tc_gemm_kernel<MODE, BF16, true><<<grid, kThreads, kSmemBytes, s>>>(dummy, dummy, dummy, dummy,
+                                                                        ep, items, tile_inst);
+  } else {
+    tc_gemm_kernel<MODE, BF16, false><<<grid, kThreads, kSmemBytes, s>>>(A->hi, A->lo, B->hi, B->lo,
+                                                                         ep, nullptr, nullptr);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 }  // namespace
@@ -656,7 +712,8 @@ int tc_launch_gemm1(const TcOperands* opX, const float* X, float* Sig, void* Sh,
   ep.ntiles = tc_num_tiles(Mp);
   ep.split_scale = split_scale;
   ep.inv_s2 = 1.0f / (split_scale * split_scale);
-  return bf16 ? launch_tc<1, true>(opX, opX, ep, s) : launch_tc<1, false>(opX, opX, ep, s);
+  return bf16 ? launch_tc<1, true, false>(opX, opX, ep, nullptr, nullptr, s)
+              : launch_tc<1, false, false>(opX, opX, ep, nullptr, nullptr, s);
 }
 
 int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X, const float* Sig,
@@ -676,9 +733,36 @@ int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X
   ep.ntiles = tc_num_tiles(Mp);
   ep.split_scale = split_scale;
   ep.inv_s2 = 1.0f / (split_scale * split_scale);
-  return bf16 ? launch_tc<2, true>(opX, opS, ep, s) : launch_tc<2, false>(opX, opS, ep, s);
+  return bf16 ? launch_tc<2, true, false>(opX, opS, ep, nullptr, nullptr, s)
+              : launch_tc<2, false, false>(opX, opS, ep, nullptr, nullptr, s);
 }
 
 void tc_set_smem_attrs() {}
+
+size_t tc_map_bytes() { return 6 * sizeof(CUtensorMap); }
+
+// Host images of the six tensor maps of one batched instance.
+int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* err, int errlen) {
+  CUtensorMap* m = (CUtensorMap*)maps_host;
+  const void* ptrs[6] = {it.Xh[0], it.Xl[0], it.Xh[1], it.Xl[1], it.Sh, it.Sl};
+  for (int k = 0; k < 6; ++k)
+    if (encode_map(&m[k], ptrs[k], it.Mp, bf16, err, errlen)) return 1;
+  return 0;
+}
+
+int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
+                         int ntiles, double* part, int bf16, float split_scale, cudaStream_t s) {
+  (void)batch;
+  Epi ep{};
+  ep.part = part;
+  ep.ntiles = ntiles;
+  ep.split_scale = split_scale;
+  ep.inv_s2 = 1.0f / (split_scale * split_scale);
+  if (mode == 1)
+    return bf16 ? launch_tc<1, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
+                : launch_tc<1, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
+  return bf16 ? launch_tc<2, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
+              : launch_tc<2, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
+}
 
 }  // namespace gcp

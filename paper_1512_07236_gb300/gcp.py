@@ -205,6 +205,42 @@ class Solver:
         info["status_code"] = st
         return out, info
 
+    def solve_batched(self, Hs, Ns, outs=None, out_dtype=None, raise_on_error=False, **opts):
+        """Independent solves of uneven size in one call.  Hs: list of square
+        CUDA tensors (same dtype), Ns: list of ints.  Returns (Ds, infos)."""
+        B = len(Hs)
+        if B == 0 or len(Ns) != B:
+            raise ValueError("need one N per H")
+        for k, H in enumerate(Hs):
+            _check_matrix(H, f"H[{k}]")
+            if H.dtype != Hs[0].dtype:
+                raise TypeError("all H must share a dtype")
+        if outs is None:
+            dt = out_dtype or (torch.float64 if opts.get("prec", "fp64") in ("fp64", 0, "mixed_fp16",
+                                                                            "mixed_bf16", 3, 4)
+                               else torch.float32)
+            outs = [torch.empty((H.shape[0], H.shape[0]), dtype=dt, device=H.device) for H in Hs]
+        for k, D in enumerate(outs):
+            _check_matrix(D, f"out[{k}]")
+            if D.stride(0) != D.shape[0]:
+                raise ValueError("batched outputs must be dense (leading dimension M)")
+        Hp = (C.c_void_p * B)(*[H.data_ptr() for H in Hs])
+        Dp = (C.c_void_p * B)(*[D.data_ptr() for D in outs])
+        Mv = (C.c_int * B)(*[H.shape[0] for H in Hs])
+        Nv = (C.c_int * B)(*[int(n) for n in Ns])
+        Lv = (C.c_int * B)(*[H.stride(0) for H in Hs])
+        res = (Result * B)()
+        o = make_options(**opts)
+        st = self.lib.gcp_solve_batched(self.h, B, Hp, Mv, Nv, Lv, _dtype_code(Hs[0]), Dp,
+                                        _dtype_code(outs[0]), res, C.byref(o))
+        allow = () if raise_on_error else (ERR_NOT_CONVERGED, ERR_ILL_CONDITIONED, ERR_NO_GAP)
+        self._check(st, allow=allow)
+        infos = []
+        for r in res:
+            d = r.as_dict()
+            infos.append(d)
+        return outs, infos
+
     def time_kernels(self, M, N, prec="fp16x3", reps=10):
         """Mean duration (ms) of GEMM1 and GEMM2 of one step, CUDA events on
         the current stream; needs a prior solve of size M on this handle."""

@@ -1,0 +1,111 @@
+"""gcp_solve_batched (through the C ABI): many Hamiltonians of uneven size
+in one call, per-instance c_n and stop test.
+
+Each instance runs the same recursion as gcp_solve on the same tiles, so a
+batched solve must equal a loop of single solves exactly, and the FP64
+batch must meet the FP64 parity bar against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import gcp_oracle as o
+from paper_1512_07236_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1512_07236_gb300 import gcp
+    return gcp.Solver()
+
+
+def _instances(seed=0):
+    """Uneven sizes (ragged tails, one instance per Mp class up to 512),
+    N = round(M/4), gaps drawn in [0.05, 0.2]."""
+    rng = np.random.default_rng(seed)
+    Ms = [64, 96, 130, 200, 256, 300, 384, 512]
+    out = []
+    for k, M in enumerate(Ms):
+        g = float(rng.uniform(0.05, 0.2))
+        N = int(round(M / 4))
+        H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -g / 2), (g / 2, 1.0), seed=100 + k)
+        out.append((H, N, eps, Q))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return _instances()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_batched_fp64_matches_oracle(solver, batch):
+    Hs = [_dev(H) for H, _, _, _ in batch]
+    Ds, infos = solver.solve_batched(Hs, [N for _, N, _, _ in batch], prec="fp64", tol=1e-12)
+    for (H, N, eps, Q), D, info in zip(batch, Ds, infos):
+        ref = o.solve(H, N, tol=1e-12)
+        assert info["status"] == 0
+        assert np.abs(D.cpu().numpy() - ref["D"]).max() <= 1e-10
+        assert abs(info["iters"] - ref["iters"]) <= 1
+        assert abs(info["energy"] - ref["E"]) <= 1e-12 * abs(ref["E"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp16", "fp16x3"])
+def test_batched_equals_loop_of_single_solves(solver, batch, prec):
+    Hs = [_dev(H) for H, _, _, _ in batch]
+    Ns = [N for _, N, _, _ in batch]
+    kw = dict(prec=prec, tol=1e-10 if prec != "fp16x3" else 1e-12)
+    Ds, infos = solver.solve_batched(Hs, Ns, **kw)
+    for H, N, D, info in zip(Hs, Ns, Ds, infos):
+        D1, i1 = solver.solve(H, N, out_dtype=D.dtype, **kw)
+        assert info["iters"] == i1["iters"] and info["status"] == i1["status"]
+        assert torch.equal(D, D1)
+
+
+def test_batched_mixed_accuracy(solver, batch):
+    Hs = [_dev(H) for H, _, _, _ in batch]
+    Ds, infos = solver.solve_batched(Hs, [N for _, N, _, _ in batch], prec="mixed_fp16",
+                                     tol=1e-10)
+    for (H, N, eps, Q), D, info in zip(batch, Ds, infos):
+        Dref = Q[:, :N] @ Q[:, :N].T
+        Dg = D.cpu().numpy()
+        assert info["status"] == 0
+        assert info["idem_fro"] <= 1e-10
+        assert abs(np.trace(Dg) - N) <= 1e-9
+        assert np.linalg.norm(Dg - Dref) / np.sqrt(N) <= 3e-6
+        assert abs(info["energy"] - eps[:N].sum()) <= 1e-9 * abs(eps[:N].sum())
+
+
+def test_batched_edge_instances_do_not_disturb_others(solver, batch):
+    """N = 0, N = M and H = mu I inside a batch: each gets its own status;
+    the others are unaffected."""
+    from paper_1512_07236_gb300 import gcp
+    H0, N0, _, _ = batch[2]
+    H1, N1, _, _ = batch[4]
+    Hs = [_dev(H0), _dev(np.eye(40) * 0.5), _dev(H1), _dev(H0), _dev(H0)]
+    Ns = [N0, 10, N1, 0, H0.shape[0]]
+    Ds, infos = solver.solve_batched(Hs, Ns, prec="fp64", tol=1e-12)
+    assert infos[1]["status"] == gcp.ERR_NO_GAP
+    assert np.abs(Ds[1].cpu().numpy() - 0.25 * np.eye(40)).max() <= 1e-15
+    assert float(Ds[3].abs().max()) == 0.0
+    assert np.array_equal(Ds[4].cpu().numpy(), np.eye(H0.shape[0]))
+    for k, (H, N) in ((0, (H0, N0)), (2, (H1, N1))):
+        D1, i1 = solver.solve(_dev(H), N, prec="fp64", tol=1e-12)
+        assert infos[k]["status"] == 0 and torch.equal(Ds[k], D1)
+
+
+def test_batched_host_loop_matches_graph(solver, batch):
+    Hs = [_dev(H) for H, _, _, _ in batch[:4]]
+    Ns = [N for _, N, _, _ in batch[:4]]
+    D1, i1 = solver.solve_batched(Hs, Ns, prec="mixed_fp16", tol=1e-10, use_graph=True)
+    D2, i2 = solver.solve_batched(Hs, Ns, prec="mixed_fp16", tol=1e-10, use_graph=False)
+    for a, b, x, y in zip(D1, D2, i1, i2):
+        assert x["iters"] == y["iters"]
+        assert torch.equal(a, b)
