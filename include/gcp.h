@@ -162,11 +162,15 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
                              int d_dtype, gcp_result* res, const gcp_options* opt);
 
 /* Reverse-mode derivative of L = <G_D, D_K> + g_E * Tr(H D_K), where D_K is
- * the iterate after exactly opt->fixed_iters steps from the guess of H.
+ * the iterate after exactly opt->fixed_iters steps of Eq. hpcp3 from the
+ * guess of H (Eq. dmguess, Eq. pmcpguess); c_n depends on D_n (Eq. mcwgamb)
+ * and the adjoint includes that dependence.  FP64 (opt->prec = GCP_FP64).
  * H: device M x M (ld, h_dtype); G_D: device M x M (ld, h_dtype) or NULL;
- * dL_dH: device M x M (ld, h_dtype), written, symmetric.  Re-runs the
- * forward pass itself, storing a checkpoint every opt->ckpt_every steps and
- * recomputing the iterates in between. */
+ * dL_dH: device M x M (ld, h_dtype), written, symmetric (the derivative with
+ * respect to a symmetric H; the Gershgorin bound contributes a subgradient).
+ * Runs the forward pass itself, keeping a checkpoint every opt->ckpt_every
+ * steps (default 8) and recomputing the iterates in between; steps past the
+ * 0/0 guard are identity steps.  0 < N < M required. */
 gcp_status gcp_backward(void* handle, const void* H, int M, int N, int ld, int h_dtype,
                         const void* G_D, double g_E, void* dL_dH, const gcp_options* opt);
 

@@ -25,7 +25,6 @@ using namespace gcp;
 namespace {
 
 constexpr float kSplitScale = 16384.0f;  // 2^14: see Split in gcp_device.cuh
-constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
 
 struct Handle {
   std::string err;
@@ -66,6 +65,8 @@ struct Handle {
   std::vector<char> bkey;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bexec = nullptr;
+  // adjoint workspace (checkpoints, segment iterates, adjoint buffers)
+  void* adj = nullptr;
 };
 
 gcp_status fail(Handle* h, gcp_status s, const char* fmt, ...) {
@@ -423,6 +424,7 @@ gcp_status gcp_destroy(void* hv) {
   if (h->bexec) cudaGraphExecDestroy(h->bexec);
   if (h->bgraph) cudaGraphDestroy(h->bgraph);
   cudaFree(h->arena);
+  adjoint_free(h->adj);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->D64[i]);
     cudaFree(h->X[i]);
@@ -972,16 +974,27 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
                         const void* G_D, double g_E, void* dL_dH, const gcp_options* opt) {
   Handle* h = (Handle*)hv;
   if (!h) return GCP_ERR_INVALID_ARG;
-  (void)H;
-  (void)M;
-  (void)N;
-  (void)ld;
-  (void)h_dtype;
-  (void)G_D;
-  (void)g_E;
-  (void)dL_dH;
-  (void)opt;
-  return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: not built yet");
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  if (!H || !dL_dH || M <= 0 || N <= 0 || N >= M || ld < M || !valid_dtype(h_dtype) ||
+      o.fixed_iters <= 0 || o.ckpt_every < 0 || !(g_E == g_E))
+    return fail(h, GCP_ERR_INVALID_ARG,
+                "gcp_backward: bad arguments (needs 0 < N < M and opt->fixed_iters > 0)");
+  if (o.prec != GCP_FP64)
+    return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: the adjoint runs in FP64 (prec = GCP_FP64)");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  gcp_status r;
+  if ((r = ensure_common(h, f64_num_tiles(M), M, o.fixed_iters + 2)) != GCP_OK) return r;
+  if ((r = ensure_f64(h, M)) != GCP_OK) return r;
+  char err[256] = {0};
+  const int rc = adjoint_backward(&h->adj, H, M, N, ld, h_dtype == GCP_F64, G_D, g_E, dL_dH,
+                                  o.fixed_iters, o.ckpt_every, h->D64[0], h->D64[1], h->S64,
+                                  h->part, h->gpart, h->st, h->hist, s, err, sizeof err);
+  if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
+  return GCP_OK;
 }
 
 gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* ms,

@@ -20,59 +20,17 @@
 // GEMM2 (P = S D) epilogue: D_{n+1} = a D + b S - 2 P with a = 1 - 2c,
 // b = 2 + 2c (Eq. hpcp3 expanded).
 #include "gcp_device.cuh"
+#include "gcp_fp64_tile.cuh"
 #include "gcp_internal.cuh"
 
 namespace gcp {
 
 namespace {
-constexpr int kThreads = 256;
-constexpr int kBK = 16;
+constexpr int kThreads = kF64Threads;
+constexpr int kBK = kF64BK;
 
 __device__ __forceinline__ void tile_coords(int t, int T, int& bi, int& bj) {
-  int i = 0;
-  while (t >= T - i) {
-    t -= T - i;
-    ++i;
-  }
-  bi = i;
-  bj = i + t;
-}
-
-// acc[i][j] = sum_k A[m0 + ty + 16 i][k] * B[k][n0 + tx + 16 j] with A, B
-// symmetric, so both slices are row reads of the operands.
-template <int BT>
-__device__ __forceinline__ void f64_mainloop(const double* __restrict__ A,
-                                             const double* __restrict__ B, int M, int ld, int m0,
-                                             int n0, double (&acc)[BT / 16][BT / 16],
-                                             double (*As)[BT], double (*Bs)[BT]) {
-  constexpr int RT = BT / 16;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int i = 0; i < RT; ++i)
-#pragma unroll
-    for (int j = 0; j < RT; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < M; k0 += kBK) {
-    for (int e = threadIdx.x; e < kBK * BT; e += kThreads) {
-      const int k = e / BT, c = e % BT;
-      const int gk = k0 + k;
-      As[k][c] = (gk < M && m0 + c < M) ? A[(size_t)gk * ld + m0 + c] : 0.0;
-      Bs[k][c] = (gk < M && n0 + c < M) ? B[(size_t)gk * ld + n0 + c] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kBK; ++k) {
-      double a[RT], b[RT];
-#pragma unroll
-      for (int i = 0; i < RT; ++i) a[i] = As[k][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < RT; ++j) b[j] = Bs[k][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < RT; ++i)
-#pragma unroll
-        for (int j = 0; j < RT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
+  f64_tile_coords(t, T, bi, bj);
 }
 
 template <int BT, typename HT>

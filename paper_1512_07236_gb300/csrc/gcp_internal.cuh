@@ -142,6 +142,14 @@ int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X
                     float split_scale, int* dev_err, cudaStream_t s);
 void tc_set_smem_attrs();
 
+// ---- adjoint (gcp_adjoint.cu) --------------------------------------------
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+int adjoint_backward(void** ws, const void* H, int M, int N, int ld, int h_f64, const void* GD,
+                     double gE, void* dLdH, int K, int ck, double* D64_0, double* D64_1,
+                     double* S64, double* part, double* gpart, State* st, double* hist,
+                     cudaStream_t s, char* err, int errlen);
+void adjoint_free(void* ws);
+
 // ---- batched solves (many instances per launch) --------------------------
 // guess: per-instance Gershgorin/trace partials (gstride slots of 4 doubles
 // per instance in `gpart`, the instance using its own gblocks of them, in

@@ -241,6 +241,27 @@ class Solver:
             infos.append(d)
         return outs, infos
 
+    def backward(self, H, N, fixed_iters, G_D=None, g_E=0.0, ckpt_every=8, out=None):
+        """dL/dH of L = <G_D, D_K> + g_E Tr(H D_K), D_K after exactly
+        `fixed_iters` FP64 steps from the guess (gcp_backward)."""
+        _check_matrix(H, "H")
+        if G_D is not None:
+            _check_matrix(G_D, "G_D")
+            if G_D.dtype != H.dtype or G_D.stride(0) != H.stride(0):
+                raise ValueError("G_D must match H's dtype and layout")
+        if out is None:
+            out = torch.empty_like(H)
+        _check_matrix(out, "out")
+        if out.dtype != H.dtype or out.stride(0) != H.stride(0):
+            raise ValueError("out must match H's dtype and layout")
+        o = make_options(prec="fp64", fixed_iters=fixed_iters, ckpt_every=ckpt_every)
+        st = self.lib.gcp_backward(self.h, C.c_void_p(H.data_ptr()), H.shape[0], int(N),
+                                   H.stride(0), _dtype_code(H),
+                                   C.c_void_p(G_D.data_ptr() if G_D is not None else 0),
+                                   float(g_E), C.c_void_p(out.data_ptr()), C.byref(o))
+        self._check(st)
+        return out
+
     def time_kernels(self, M, N, prec="fp16x3", reps=10):
         """Mean duration (ms) of GEMM1 and GEMM2 of one step, CUDA events on
         the current stream; needs a prior solve of size M on this handle."""
