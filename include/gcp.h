@@ -65,9 +65,10 @@ typedef enum { GCP_F64 = 0, GCP_F32 = 1 } gcp_dtype;
  *                   shifted state X = D - theta I held in FP32; stops at
  *                   its own accuracy floor.
  *   GCP_BF16X3      as FP16X3 with BF16 halves.
- *   GCP_MIXED_FP16  FP16X3 until the residual stagnates, then FP64 steps
- *                   until the stop test holds.
- *   GCP_MIXED_BF16  BF16X3 bulk, FP64 refinement.                       */
+ *   GCP_MIXED_FP16  FP16X3 until the residual stagnates, then refinement
+ *                   steps in FP64 arithmetic until the stop test holds
+ *                   (gcp_options.refine picks how their products run).
+ *   GCP_MIXED_BF16  BF16X3 bulk, the same refinement.                    */
 typedef enum {
   GCP_FP64 = 0,
   GCP_FP16X3 = 1,
@@ -93,6 +94,12 @@ typedef struct {
   int use_graph;       /* 1 (default): device-side loop in one CUDA graph;
                           0: host-driven loop (debugging) */
   void* stream;        /* cudaStream_t; NULL = legacy default stream */
+  int refine;          /* mixed modes, refinement products: 0 (default) exact
+                          digit-slice products on the tensor cores with
+                          McWeeny steps (M <= 29000, no fixed_iters;
+                          gcp_solve only);  1 FP64 SIMT products and HPCP
+                          steps (always used otherwise, and by
+                          gcp_solve_batched) */
 } gcp_options;
 
 typedef struct {

@@ -67,7 +67,42 @@ struct Handle {
   cudaGraphExec_t bexec = nullptr;
   // adjoint workspace (checkpoints, segment iterates, adjoint buffers)
   void* adj = nullptr;
+  // exact-slice refinement: nine digit slices of D, row scales, BF16 halves
+  // of D and of X = D^2 - D with their tensor maps
+  int oz_mp = 0;
+  void* oz_slices[kOzSlices] = {nullptr};
+  double* oz_rscale = nullptr;
+  double* oz_xscale = nullptr;
+  void* oz_dh = nullptr;
+  void* oz_dl = nullptr;
+  void* oz_xh = nullptr;
+  void* oz_xl = nullptr;
+  OzOperands* oz_op = nullptr;
+  TcOperands* oz_opD = nullptr;
+  TcOperands* oz_opX = nullptr;
 };
+
+void free_oz(Handle* h) {
+  for (int k = 0; k < kOzSlices; ++k) {
+    cudaFree(h->oz_slices[k]);
+    h->oz_slices[k] = nullptr;
+  }
+  cudaFree(h->oz_rscale);
+  cudaFree(h->oz_xscale);
+  h->oz_xscale = nullptr;
+  cudaFree(h->oz_dh);
+  cudaFree(h->oz_dl);
+  cudaFree(h->oz_xh);
+  cudaFree(h->oz_xl);
+  h->oz_rscale = nullptr;
+  h->oz_dh = h->oz_dl = h->oz_xh = h->oz_xl = nullptr;
+  if (h->oz_op) oz_free_operands(h->oz_op);
+  if (h->oz_opD) tc_free_operands(h->oz_opD);
+  if (h->oz_opX) tc_free_operands(h->oz_opX);
+  h->oz_op = nullptr;
+  h->oz_opD = h->oz_opX = nullptr;
+  h->oz_mp = 0;
+}
 
 gcp_status fail(Handle* h, gcp_status s, const char* fmt, ...) {
   if (h) {
@@ -191,6 +226,27 @@ gcp_status ensure_split(Handle* h, int Mp, int bf16) {
   return GCP_OK;
 }
 
+gcp_status ensure_oz(Handle* h, int Mp) {
+  if (Mp == h->oz_mp) return GCP_OK;
+  drop_graph(h);
+  free_oz(h);
+  const size_t n = (size_t)Mp * Mp;
+  for (int k = 0; k < kOzSlices; ++k) CK(cudaMalloc(&h->oz_slices[k], n * 2));
+  CK(cudaMalloc((void**)&h->oz_rscale, (size_t)Mp * sizeof(double)));
+  CK(cudaMalloc((void**)&h->oz_xscale, (size_t)Mp * sizeof(double)));
+  CK(cudaMalloc(&h->oz_dh, n * 2));
+  CK(cudaMalloc(&h->oz_dl, n * 2));
+  CK(cudaMalloc(&h->oz_xh, n * 2));
+  CK(cudaMalloc(&h->oz_xl, n * 2));
+  char err[256] = {0};
+  if (oz_make_operands(&h->oz_op, h->oz_slices, Mp, err, sizeof err) ||
+      tc_make_operands(&h->oz_opD, h->oz_dh, h->oz_dl, Mp, 0, err, sizeof err) ||
+      tc_make_operands(&h->oz_opX, h->oz_xh, h->oz_xl, Mp, 0, err, sizeof err))
+    return fail(h, GCP_ERR_CUDA, "%s", err);
+  h->oz_mp = Mp;
+  return GCP_OK;
+}
+
 bool is_split(int prec) { return prec >= GCP_FP16X3 && prec <= GCP_MIXED_BF16; }
 bool is_mixed(int prec) { return prec == GCP_MIXED_FP16 || prec == GCP_MIXED_BF16; }
 int split_bf16(int prec) { return prec == GCP_BF16X3 || prec == GCP_MIXED_BF16; }
@@ -230,6 +286,32 @@ gcp_status rec_f64_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
   launch_f64_gemm2(h->S64, h->D64[src], h->D64[src ^ 1], M, ld, h->st, s);
   CK(cudaPeekAtLastError());
   return GCP_OK;
+}
+
+// One refinement step with exact digit-slice products: slice D -> S = D^2
+// (exact) -> traces and ||S - D|| -> control -> D+ = S - 2 (S - D) D - a (S - D)
+// (a = 1 - 2c = 0 for the McWeeny step, small when c restores the trace).
+gcp_status rec_oz_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
+                       cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
+  const int M = a.M, Mp = h->oz_mp;
+  launch_oz_slice(h->D64[src], M, Mp, h->oz_slices, h->oz_rscale, h->oz_dh, h->oz_dl, h->st, s);
+  if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, Mp, h->st, s))
+    return fail(h, GCP_ERR_CUDA, "slice GEMM launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  launch_oz_finalize(h->S64, h->D64[src], M, Mp, h->part, h->oz_xh, h->oz_xl, h->oz_xscale,
+                     h->st, s);
+  launch_control(h->part, oz_finalize_blocks(M), h->st, a.o.history_cap > 0 ? h->hist : nullptr,
+                 ctl, (unsigned long long)cond, use_cond, s);
+  if (tc_launch_mcweeny64(h->oz_opX, h->oz_opD, h->S64, h->D64[src], h->D64[src ^ 1],
+                          h->oz_xscale, h->oz_rscale, M, Mp, h->st, s))
+    return fail(h, GCP_ERR_CUDA, "McWeeny product launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  CK(cudaPeekAtLastError());
+  return GCP_OK;
+}
+
+bool use_oz(const SolveArgs& a) {
+  return is_mixed(a.o.prec) && a.o.refine == 0 && a.o.fixed_iters == 0 && a.M <= 29000;
 }
 
 // One step of the split phase on the shifted state.
@@ -323,9 +405,12 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
     launch_phase_begin(h->st, 0, s);
   }
   if (!split || mixed) {
-    const Ctl ctl = make_ctl(a, 0, 1);
+    Ctl ctl = make_ctl(a, 0, 1);
+    const bool oz = use_oz(a);
+    ctl.mcw_only = oz ? 1 : 0;
     auto step = [&](int src, cudaGraphConditionalHandle c, cudaStream_t ss) {
-      return rec_f64_step(h, a, src, ctl, c, graph ? 1 : 0, ss);
+      return oz ? rec_oz_step(h, a, src, ctl, c, graph ? 1 : 0, ss)
+                : rec_f64_step(h, a, src, ctl, c, graph ? 1 : 0, ss);
     };
     if (graph) {
       gcp_status r = rec_while(h, s, step);
@@ -425,6 +510,7 @@ gcp_status gcp_destroy(void* hv) {
   if (h->bgraph) cudaGraphDestroy(h->bgraph);
   cudaFree(h->arena);
   adjoint_free(h->adj);
+  free_oz(h);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->D64[i]);
     cudaFree(h->X[i]);
@@ -600,9 +686,11 @@ gcp_status gcp_solve(void* hv, const void* H, int M, int N, int ld, int h_dtype,
   size_t nt = 1;
   if (split) nt = tc_num_tiles(tc_pad(M));
   if (!split || mixed) nt = nt > (size_t)f64_num_tiles(M) ? nt : (size_t)f64_num_tiles(M);
+  if (use_oz(a)) nt = nt > (size_t)oz_finalize_blocks(M) ? nt : (size_t)oz_finalize_blocks(M);
   if ((r = ensure_common(h, nt, M, o.history_cap)) != GCP_OK) return r;
   if (split && (r = ensure_split(h, tc_pad(M), split_bf16(o.prec))) != GCP_OK) return r;
   if ((!split || mixed) && (r = ensure_f64(h, M)) != GCP_OK) return r;
+  if (use_oz(a) && (r = ensure_oz(h, tc_pad(M))) != GCP_OK) return r;
   if (o.use_graph) {
     std::vector<char> key = make_key(a);
     if (!h->exec || key != h->key) {

@@ -87,7 +87,10 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
     if (crit <= ctl.tol) {
       stop = 1;
       kind = 1;
-    } else if (ctl.phase == 0 && R < 1e-8 && R >= st->Rp0 && st->Rp0 >= st->Rp1) {
+    } else if (ctl.phase == 0 && ((R < 1e-8 && R >= st->Rp0 && st->Rp0 >= st->Rp1) ||
+                                  (ctl.mcw_only && R > 0.5 * st->Rp0))) {
+      // stagnation (the slice refinement: a step that does not halve R has
+      // reached the accuracy of its products)
       stop = 1;
       kind = 3;
       status = (R <= ctl.tol) ? GCP_OK : GCP_ERR_NOT_CONVERGED;
@@ -110,7 +113,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
   // trace it also removes the rounding drift of Tr D (the eigenvalues go to
   // exactly 0 or 1).  The same switch applies while that drift is not small
   // against Tr(D - D^2).  The plain FP64 path keeps the oracle's rule.
-  const bool mcw = ctl.endgame && ctl.fixed_iters == 0 &&
+  const bool mcw = ctl.mcw_only || ctl.endgame && ctl.fixed_iters == 0 &&
                    (R < 0.05 || fabs(T1 - (double)ctl.N) > 0.05 * fabs(den));
   if (!stop) {
     // 0/0 guard.  FP64: 16 M u max(1, Tr D) (as in the oracle).  Split phase:
@@ -118,6 +121,17 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
     // 16 sqrt(M) u_32.
     const double den_min = ctl.phase == 1 ? 16.0 * sqrt((double)ctl.M) * ctl.u
                                           : 16.0 * (double)ctl.M * ctl.u * fmax(1.0, T1);
+    // Refinement endgame: the McWeeny step leaves Tr D+ = 3 T2 - 2 T3, off N
+    // by the second-order imbalance of the eigenvalue errors (up to ~3 R^2).
+    // The step of Eq. hpcp3 with 1 - 2c = (N - 3 T2 + 2 T3) / (T1 - T2) has
+    // Tr D+ = N exactly; it is taken when that c lies within 1/2 +- 0.05,
+    // where it converges like the McWeeny step.  Near idempotency the
+    // eigenvalues sit on both sides of 0 and 1, so T1 - T2 may be negative.
+    double c_mcw = 0.5;
+    if (mcw && ctl.phase == 0 && ctl.endgame && fabs(den) > den_min) {
+      const double g = ((double)ctl.N - (3.0 * T2 - 2.0 * T3)) / den;
+      if (fabs(g) <= 0.1) c_mcw = 0.5 * (1.0 - g);
+    }
     if (den <= den_min && !mcw) {
       if (ctl.fixed_iters > 0) {
         st->apply = 0;  // identity step
@@ -150,7 +164,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       // drift of the trace, c = (num + (Tr D - N)/2) / den, so that
       // Tr D_{n+1} = N for the traces as computed (exact arithmetic gives
       // Tr D_n = N and the plain Eq. mcwgamb).  FP64: Eq. mcwgamb.
-      const double c = mcw ? 0.5
+      const double c = mcw ? c_mcw
                            : (ctl.phase == 1 ? (num + 0.5 * (T1 - (double)ctl.N)) / den
                                              : num / den);
       if (n == 0 && !(c >= 0.0 && c <= 1.0) && ctl.fixed_iters == 0) {

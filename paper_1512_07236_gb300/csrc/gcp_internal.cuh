@@ -43,6 +43,7 @@ struct Ctl {
   int phase;        // 1 split precision, 0 FP64
   int final_phase;  // this phase decides the final status
   int endgame;      // McWeeny endgame (split and refinement phases only)
+  int mcw_only;     // every step is a McWeeny step (exact-slice refinement)
   double tol;
   double u;         // unit roundoff of the phase's state (den guard)
 };
@@ -128,6 +129,9 @@ void launch_convert(const void* in, int in_f64, int ldi, void* out, int out_f64,
 struct TcOperands;  // opaque: tensor maps for one (hi, lo) pair
 int tc_pad(int M);
 int tc_num_tiles(int Mp);
+// Tensor map (CUtensorMap) of an Mp x Mp 16-bit row-major operand, 128 x 32
+// boxes, 64-byte swizzle.
+int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen);
 // Build tensor maps for a pair of split halves (Mp x Mp, row-major).
 int tc_make_operands(TcOperands** op, const void* hi, const void* lo, int Mp, int bf16,
                      char* err, int errlen);
@@ -141,6 +145,34 @@ int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X
                     float* Xn, void* Xnh, void* Xnl, int M, int Mp, State* st, int bf16,
                     float split_scale, int* dev_err, cudaStream_t s);
 void tc_set_smem_attrs();
+// Refinement step (FP64): Dn = S - 2 Z - a (S - D) with Z = X D from the
+// fp16 halves of X = S - D (opX, row i scaled by xscale_i) and of D (opD,
+// row j scaled by kRefScale / dscale_j), and a = State::a (0 for the
+// McWeeny step).
+int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const double* S64,
+                        const double* D64, double* Dn64, const double* xscale,
+                        const double* dscale, int M, int Mp, State* st, cudaStream_t s);
+
+// ---- exact slice products (gcp_ozaki.cu) ---------------------------------
+// D (FP64, M x M) -> per-row scale 2^e_i with |D_ij| <= 2^e_i / 2, nine
+// signed base-32 digit slices (fp16, Mp x Mp) and the fp16 halves of
+// kRefScale D_ij / 2^e_i (the D operand of the refinement product).
+constexpr int kOzSlices = 9;
+constexpr double kRefScale = 16384.0;  // 2^14
+struct OzOperands;  // opaque: tensor maps of the nine slices
+int oz_make_operands(OzOperands** op, void* const* slices, int Mp, char* err, int errlen);
+void oz_free_operands(OzOperands* op);
+void launch_oz_slice(const double* D, int M, int Mp, void* const* slices, double* rscale,
+                     void* Dh, void* Dl, const State* st, cudaStream_t s);
+// S = D D exactly up to the slicing (FP64 out, M x M, both triangles).
+int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int M, int Mp,
+                   State* st, cudaStream_t s);
+// Partials (Tr D, Tr S, sum S o D, ||S - D||^2, 0) per block for the control
+// kernel, and the fp16 halves of xscale_i X_ij, X = S - D, with a power of
+// two xscale_i per row (max_j |xscale_i X_ij| < 2^13).
+int oz_finalize_blocks(int M);
+void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
+                        void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s);
 
 // ---- adjoint (gcp_adjoint.cu) --------------------------------------------
 constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24

@@ -1,0 +1,449 @@
+// Exact slice products for the FP64 refinement of the mixed modes.
+//
+// GB300 runs FP64 on SIMT units at ~1.2 TFLOP/s; one FP64 D^2 at M = 8192
+// takes ~0.45 s.  Here D^2 is formed on the tensor cores without rounding:
+//   * each row i of D is scaled by 2^e_i with |D_ij| <= 2^e_i / 2 and cut
+//     into nine signed base-32 digits, D_ij = 2^e_i sum_s d_s 32^-(s+1) + r,
+//     |d_s| <= 16, |r| <= 2^e_i 32^-9 / 2 (a 46-bit fixed-point value);
+//     digits are small integers, exact in fp16;
+//   * (D D)_ij = 2^(e_i+e_j) sum_w 32^-(w+2) sum_{s+t=w} sum_k d_s(i,k) d_t(j,k)
+//     for weights w = 0..9; the dropped weights (w >= 10) and the cut r each
+//     add ~1e-14 per element at M = 8192, ~2e-10 to ||D^2 - D||_F.  Those
+//     errors have random signs except on the diagonal, where the square
+//     d_5(i,k)^2 of weight 10 is always positive: dropping it would bias
+//     Tr D^2 by ~ -5e-9 at M = 8192, so the pair (5, 5) is kept too;
+//   * a pass accumulates one weight over at most P pairs with
+//     P * 256 * M <= 2^24, so every partial sum is an integer below 2^24 and
+//     the FP32 tensor-core accumulation is exact whatever its rounding mode
+//     (at M = 8192 the cap is 8 pairs: weight 8, with 9 pairs, takes two
+//     passes; larger M splits more weights);
+//   * each pass's integer sums are scaled and added in FP64.
+// The result carries the ~2^-46 slicing error of the row scales, against
+// 2^-53 for native FP64, at tensor-core speed.
+//
+// Kernel layout: persistent CTAs over the 128 x 256 tiles of the upper block
+// triangle; warp 0 issues TMA loads of one digit slice of the A rows and one
+// of the B rows per stage (8-stage ring of 24 KB stages), warp 1 issues one
+// MMA per 16-wide K step into one of two TMEM buffers (one buffer per pass,
+// so the MMAs of the next pass overlap the drain of this one), warps 2-9
+// drain each pass into the FP64 output.
+#include <stdio.h>
+#include <string.h>
+
+#include "gcp_device.cuh"
+#include "gcp_internal.cuh"
+#include "gcp_tc_ptx.cuh"
+
+namespace gcp {
+
+struct OzMaps {
+  CUtensorMap m[kOzSlices];
+};
+struct OzOperands {
+  OzMaps maps;
+};
+// The passes of one product: weight w, pairs (s, w - s) for s in
+// [s0, s0 + ns).
+constexpr int kOzMaxPass = 64;
+struct OzPlan {
+  int npass;
+  int w[kOzMaxPass];
+  int s0[kOzMaxPass];
+  int ns[kOzMaxPass];
+};
+// The slice arrays' device addresses, passed by value.
+struct OzSlicePtrs {
+  __half* p[kOzSlices];
+};
+
+namespace {
+using namespace tcx;
+constexpr int BM = 128, BN = 256, BK = 32, STAGES = 8;
+constexpr int kThreads = 320;
+constexpr uint32_t kABytes = BM * BK * 2;          // 8 KB
+constexpr uint32_t kBBytes = BN * BK * 2;          // 16 KB
+constexpr uint32_t kStageBytes = kABytes + kBBytes;  // 24 KB
+constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxW = kOzSlices;  // weights 0..9
+
+__device__ __forceinline__ void oz_tile(int t, int NI, int NJ, int& I, int& J) {
+  int j = 0;
+  while (true) {
+    const int cnt = (2 * j + 2 < NI ? 2 * j + 2 : NI);
+    if (t < cnt || j + 1 >= NJ) {
+      I = t;
+      J = j;
+      return;
+    }
+    t -= cnt;
+    ++j;
+  }
+}
+
+// ---- slicing ---------------------------------------------------------------
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ D, int M, int Mp,
+                                                       const OzSlicePtrs slices,
+                                                       double* __restrict__ rscale,
+                                                       __half* __restrict__ Dh,
+                                                       __half* __restrict__ Dl,
+                                                       const State* __restrict__ st) {
+  if (st->stopped) return;
+  __shared__ double red[32];
+  __shared__ double scale_sh;
+  const int i = blockIdx.x;
+  double mx = 0.0;
+  if (i < M)
+    for (int j = threadIdx.x; j < M; j += blockDim.x) mx = fmax(mx, fabs(D[(size_t)i * M + j]));
+  // block max
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    // smallest power of two with m <= 2^e / 2
+    int e = 0;
+    if (m > 0.0) {
+      frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+      e += 1;
+    }
+    scale_sh = ldexp(1.0, e);
+    rscale[i] = scale_sh;
+  }
+  __syncthreads();
+  const double inv = 1.0 / scale_sh;  // exact: a power of two
+  for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
+    const double d = (i < M && j < M) ? D[(size_t)i * M + j] : 0.0;
+    double v = d * inv;  // |v| <= 1/2
+    // fp16 halves of 2^14 v (|.| <= 2^13) for the refinement product
+    const double vs = v * kRefScale;
+    const __half h = __double2half(vs);
+    Dh[(size_t)i * Mp + j] = h;
+    Dl[(size_t)i * Mp + j] = __double2half(vs - (double)__half2float(h));
+#pragma unroll
+    for (int s = 0; s < kOzSlices; ++s) {
+      const double t = v * 32.0;
+      const double dg = rint(t);  // |dg| <= 16
+      v = t - dg;                 // exact
+      slices.p[s][(size_t)i * Mp + j] = __double2half((float)dg);
+    }
+  }
+}
+
+// ---- finalize: traces, residual, halves of X = S - D -----------------------
+// Row i of X is scaled by xscale_i = 2^(13 - e) with max_j |X_ij| < 2^e, so
+// that its fp16 halves keep ~22 bits of every row whatever the size of X.
+constexpr int kFinThreads = 256;
+__global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
+    const double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
+    double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
+    double* __restrict__ xscale, const State* __restrict__ st) {
+  if (st->stopped) return;
+  __shared__ double red[32 * 5];
+  __shared__ double mred[32];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = blockIdx.x; i < Mp; i += gridDim.x) {
+    double mx = 0.0;
+    if (i < M)
+      for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const size_t o = (size_t)i * M + j;
+        const double sv = S[o], dv = D[o];
+        const double x = sv - dv;
+        if (i == j) {
+          v[0] += dv;
+          v[1] += sv;
+        }
+        v[2] += sv * dv;
+        v[3] += x * x;
+        mx = fmax(mx, fabs(x));
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < kFinThreads / 32; ++w) m = fmax(m, mred[w]);
+    __syncthreads();  // mred is reused by the next row
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);  // m < 2^e
+    const double sx = ldexp(1.0, 13 - e);
+    if (threadIdx.x == 0) xscale[i] = sx;
+    for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
+      double x = 0.0;
+      if (i < M && j < M) {
+        const size_t o = (size_t)i * M + j;
+        x = (S[o] - D[o]) * sx;
+      }
+      const __half h = __double2half(x);
+      Xh[(size_t)i * Mp + j] = h;
+      Xl[(size_t)i * Mp + j] = __double2half(x - (double)__half2float(h));
+    }
+  }
+  block_sum<5>(v, red);
+  if (threadIdx.x == 0) {
+    double* p = part + (size_t)blockIdx.x * kPartFields;
+    for (int k = 0; k < 5; ++k) p[k] = v[k];
+    p[5] = 0.0;
+  }
+}
+
+// ---- the exact slice GEMM ---------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ OzPlan plan,
+                   const double* __restrict__ rscale, double* __restrict__ S, int M, int Mp,
+                   int ntiles, State* st) {
+  if (st->stopped || st->timeout) return;
+  const int NI = Mp / BM, NJ = Mp / BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_holder;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], kDrainThreads / 32);
+    }
+    mbar_init(&fin_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_holder)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  const int nkb = Mp / BK;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        int I, J;
+        oz_tile(t, NI, NJ, I, J);
+        for (int ps = 0; ps < plan.npass && alive; ++ps)
+          for (int p = plan.s0[ps]; p < plan.s0[ps] + plan.ns[ps] && alive; ++p)
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+              const int w = plan.w[ps];
+              const uint32_t s = g % STAGES;
+              if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1)) {
+                atomicOr(&st->timeout, 1);
+                alive = false;
+                break;
+              }
+              const uint32_t stage = sbase + s * kStageBytes;
+              mbar_expect_tx(&full_bar[s], kStageBytes);
+              const int kx = kb * BK;
+              tma_load_2d(&maps.m[p], &full_bar[s], stage, kx, I * BM);
+              tma_load_2d(&maps.m[w - p], &full_bar[s], stage + kABytes, kx, J * BN);
+              tma_load_2d(&maps.m[w - p], &full_bar[s], stage + kABytes + kBBytes / 2, kx,
+                          J * BN + 128);
+            }
+      }
+      const uint32_t first = g > STAGES ? g - STAGES : 0;
+      for (uint32_t k = first; k < g; ++k)
+        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(&st->timeout, 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(0);
+      uint32_t g = 0, qc = 0;
+      bool alive = true;
+      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        for (int ps = 0; ps < plan.npass && alive; ++ps, ++qc) {
+          const uint32_t b = qc & 1;
+          if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
+            atomicOr(&st->timeout, 1);
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = tmem + b * 256;
+          bool first = true;
+          for (int p = plan.s0[ps]; p < plan.s0[ps] + plan.ns[ps] && alive; ++p)
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+              const uint32_t s = g % STAGES;
+              if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
+                atomicOr(&st->timeout, 1);
+                alive = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a = sbase + s * kStageBytes;
+              const uint32_t bb = a + kABytes;
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                umma(acc, sdesc(a + off), sdesc(bb + off), idesc, first ? 0u : 1u);
+                first = false;
+              }
+              umma_commit(&empty_bar[s]);
+            }
+          umma_commit(&accf_bar[b]);
+        }
+      }
+      umma_commit(&fin_bar);
+      if (!mbar_wait(&fin_bar, 0)) atomicOr(&st->timeout, 1);
+    }
+  } else {
+    const int dw = warp - 2, q = warp & 3, half = dw >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    uint32_t qc = 0;
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      int I, J;
+      oz_tile(t, NI, NJ, I, J);
+      const int row = I * BM + 32 * q + lane;
+      const int jb = 2 * J + half, c_base = J * BN + half * 128;
+      const bool need = jb >= I, diag = jb == I;
+      const double rs_row = row < M ? rscale[row] : 0.0;
+      for (int ps = 0; ps < plan.npass; ++ps, ++qc) {
+        const double wscale = ldexp(1.0, -5 * (plan.w[ps] + 2));  // 32^-(w+2)
+        const bool first_pass = ps == 0;
+        const uint32_t b = qc & 1;
+        const bool got = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1));
+        if (!got) {
+          if (lane == 0) atomicOr(&st->timeout, 1);
+          alive = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + lane_base + b * 256 + half * 128;
+#pragma unroll
+        for (int part = 0; part < 4; ++part) {
+          uint32_t r[32];
+          tmem_ld32(base + part * 32, r);
+          tmem_ld_wait();
+          if (need && row < M) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const int c = c_base + part * 32 + k;
+              if (c >= M || (diag && c < row)) continue;
+              const double v = (double)__uint_as_float(r[k]) * wscale * rs_row * rscale[c];
+              double* dst = S + (size_t)row * M + c;
+              *dst = first_pass ? v : *dst + v;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[b]);
+      }
+      // mirror the finished tile (each thread re-reads its own stores)
+      if (alive && need && row < M) {
+        for (int k = 0; k < 128; ++k) {
+          const int c = c_base + k;
+          if (c >= M || (diag && c <= row)) continue;
+          S[(size_t)c * M + row] = S[(size_t)row * M + c];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n > 0) return n;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    n = 148;
+  return n;
+}
+}  // namespace
+
+int oz_make_operands(OzOperands** op, void* const* slices, int Mp, char* err, int errlen) {
+  OzOperands* o = new OzOperands;
+  for (int s = 0; s < kOzSlices; ++s)
+    if (tc_encode_map(&o->maps.m[s], slices[s], Mp, 0, err, errlen)) {
+      delete o;
+      return 1;
+    }
+  *op = o;
+  return 0;
+}
+
+void oz_free_operands(OzOperands* op) { delete op; }
+
+void launch_oz_slice(const double* D, int M, int Mp, void* const* slices, double* rscale,
+                     void* Dh, void* Dl, const State* st, cudaStream_t s) {
+  OzSlicePtrs sp;
+  for (int k = 0; k < kOzSlices; ++k) sp.p[k] = (__half*)slices[k];
+  oz_slice_kernel<<<Mp, 256, 0, s>>>(D, M, Mp, sp, rscale, (__half*)Dh, (__half*)Dl, st);
+}
+
+// Passes for an M-long inner dimension: weights 0..9, pairs (s, w - s)
+// with 0 <= s, w - s < kOzSlices, at most floor(2^24 / (256 M)) pairs a pass.
+int oz_plan(int M, OzPlan* plan) {
+  const long long cap = (1ll << 24) / (256ll * M);
+  if (cap < 1) return 1;
+  plan->npass = 0;
+  for (int w = 0; w <= kMaxW; ++w) {
+    int lo = w - (kOzSlices - 1) > 0 ? w - (kOzSlices - 1) : 0;
+    const int hi = w < kOzSlices - 1 ? w : kOzSlices - 1;
+    while (lo <= hi) {
+      const int n = (hi - lo + 1) < cap ? (hi - lo + 1) : (int)cap;
+      if (plan->npass >= kOzMaxPass) return 1;
+      plan->w[plan->npass] = w;
+      plan->s0[plan->npass] = lo;
+      plan->ns[plan->npass] = n;
+      ++plan->npass;
+      lo += n;
+    }
+  }
+  // the first dropped square, (5, 5) of weight 10 (see the top of the file)
+  if (plan->npass >= kOzMaxPass) return 1;
+  plan->w[plan->npass] = kMaxW + 1;
+  plan->s0[plan->npass] = (kMaxW + 1) / 2;
+  plan->ns[plan->npass] = 1;
+  ++plan->npass;
+  return 0;
+}
+
+int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int M, int Mp,
+                   State* st, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess)
+      return 1;
+    attr = true;
+  }
+  const int ntiles = tc_num_tiles(Mp);
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  OzPlan plan;
+  if (oz_plan(M, &plan)) return 1;
+  oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(op->maps, plan, rscale, S64, M, Mp, ntiles,
+                                                    st);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+int oz_finalize_blocks(int M) { return M < 1024 ? M : 1024; }
+
+void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
+                        void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s) {
+  oz_finalize_kernel<<<oz_finalize_blocks(M), kFinThreads, 0, s>>>(
+      S64, D64, M, Mp, part, (__half*)Xh, (__half*)Xl, xscale, st);
+}
+
+}  // namespace gcp

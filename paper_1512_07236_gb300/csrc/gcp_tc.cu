@@ -45,6 +45,7 @@
 
 #include "gcp_device.cuh"
 #include "gcp_internal.cuh"
+#include "gcp_tc_ptx.cuh"
 
 namespace gcp {
 
@@ -54,16 +55,15 @@ struct TcOperands {
 };
 
 namespace {
+using namespace tcx;
 constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
 constexpr int KC_STAGES = 2;  // K chunk per TMEM drain = KC_STAGES * BK = 64
 constexpr int kThreads = 320;
-constexpr int kDrainThreads = 256;
 constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
 constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct Epi {
   const float* X;    // current shifted iterate (FP32, Mp x Mp)
@@ -78,111 +78,15 @@ struct Epi {
   int M, Mp, ntiles;
   float split_scale;  // s
   float inv_s2;       // 1/s^2
+  // mode 3 (McWeeny refinement in FP64): D+ = S - 2 Z - a (S - D),
+  // Z = (S - D) D, a = 1 - 2c from the state
+  const double* S64;
+  const double* D64;
+  double* Dn64;
+  const double* rs_x;  // row scales of the X operand
+  const double* rs_d;  // 2^e_j: row j of the D operand holds kRefScale D_jk / 2^e_j
+  int ld64;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on the phase of `bar` with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > kWaitNs) return false;
-  }
-}
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, uint32_t dst,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4}], [%2];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major, SWIZZLE_64B (64-byte rows,
-// 8-row groups 512 B apart = SBO), descriptor version 1 (bits 46-47).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;             // LBO (ignored for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;    // SBO
-  d |= (uint64_t)1 << 46;             // version
-  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
-  return d;
-}
-// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A/B format
-// (bits 7-9, 10-12: 0 fp16, 1 bf16), both K-major, N>>3 at bit 17,
-// M>>4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_f16(int bf16) {
-  return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
-}
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                     uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void drain_bar_sync() {
-  asm volatile("bar.sync 1, %0;" ::"r"(kDrainThreads) : "memory");
-}
 
 // Linear tile index -> (I, J): I a 128-row block, J a 256-column block,
 // kept when the tile reaches the upper block triangle (2J + 1 >= I).
@@ -208,6 +112,27 @@ __device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base,
                                              const float (&acc)[128], bool mma_valid,
                                              float ca, float cb, float cj, double (&dpart)[5]) {
   using HT = typename Split<BF16>::T;
+  if constexpr (MODE == 3) {
+    // McWeeny refinement step in FP64 (Eq. mcweeny3): with S = D^2 exact
+    // and X = S - D small, 3D^2 - 2D^3 = S - 2 X D; the product Z = X D only
+    // needs the relative accuracy of the split product because |X| is small.
+    // The general step of Eq. hpcp3 is the same plus (1 - 2c)(D - S); the
+    // control kernel sets c within 1/2 +- 0.05 to put Tr D+ back at N.
+    if (row >= ep.M) return;
+    const double wr = 1.0 / (kRefScale * ep.rs_x[row]);  // powers of two: exact
+    const double g = ep.st->a;
+#pragma unroll
+    for (int k = 0; k < 128; ++k) {
+      const int c = c_base + k;
+      if (c >= ep.M || (diag_blk && c < row)) continue;
+      const size_t o = (size_t)row * ep.ld64 + c;
+      const double sv = ep.S64[o];
+      const double v = sv - 2.0 * (wr * ep.rs_d[c]) * (double)acc[k] - g * (sv - ep.D64[o]);
+      ep.Dn64[o] = v;
+      if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
+    }
+    return;
+  }
   const int Mp = ep.Mp;
   const double th = ep.st->theta;
   const float f2th = (float)(2.0 * th);
@@ -673,6 +598,10 @@ int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const Bat
 
 int tc_pad(int M) { return ((M + BN - 1) / BN) * BN; }
 
+int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen) {
+  return encode_map((CUtensorMap*)map, ptr, Mp, bf16, err, errlen);
+}
+
 int tc_num_tiles(int Mp) {
   const int NI = Mp / BM, NJ = Mp / BN;
   int n = 0;
@@ -738,6 +667,25 @@ int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X
 }
 
 void tc_set_smem_attrs() {}
+
+int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const double* S64,
+                        const double* D64, double* Dn64, const double* xscale,
+                        const double* dscale, int M, int Mp, State* st, cudaStream_t s) {
+  Epi ep{};
+  ep.st = st;
+  ep.M = M;
+  ep.Mp = Mp;
+  ep.ntiles = tc_num_tiles(Mp);
+  ep.split_scale = 1.0f;
+  ep.inv_s2 = 1.0f;
+  ep.S64 = S64;
+  ep.D64 = D64;
+  ep.Dn64 = Dn64;
+  ep.rs_x = xscale;
+  ep.rs_d = dscale;
+  ep.ld64 = M;
+  return launch_tc<3, false, false>(opX, opD, ep, nullptr, nullptr, s);
+}
 
 size_t tc_map_bytes() { return 6 * sizeof(CUtensorMap); }
 

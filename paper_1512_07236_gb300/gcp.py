@@ -32,7 +32,8 @@ EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destro
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("stop", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("fixed_iters", C.c_int), ("ckpt_every", C.c_int),
-                ("history_cap", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p)]
+                ("history_cap", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p),
+                ("refine", C.c_int)]
 
 
 class Result(C.Structure):
@@ -113,7 +114,8 @@ def _check_matrix(t: torch.Tensor, name: str):
 
 
 def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_iters=0,
-                 ckpt_every=8, history_cap=0, use_graph=True, stream=None) -> Options:
+                 ckpt_every=8, history_cap=0, use_graph=True, stream=None,
+                 refine="slices") -> Options:
     lib = load_library()
     o = Options()
     lib.gcp_default_options(C.byref(o))
@@ -125,6 +127,7 @@ def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_it
     o.ckpt_every = int(ckpt_every)
     o.history_cap = int(history_cap)
     o.use_graph = 1 if use_graph else 0
+    o.refine = {"slices": 0, "fp64": 1}[refine] if isinstance(refine, str) else int(refine)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

@@ -54,15 +54,18 @@ def test_single_split_step(solver, prec, tol, M):
     assert err <= tol * max(1.0, np.abs(Dn).max()), err
 
 
+@pytest.mark.parametrize("refine", ["slices", "fp64"])
 @pytest.mark.parametrize("prec", ["mixed_fp16", "mixed_bf16"])
 @pytest.mark.parametrize("M,N,gap,seed", [(256, 64, 0.2, 1), (512, 128, 0.1, 2), (700, 175, 0.05, 3)])
-def test_mixed_solve_parity(solver, prec, M, N, gap, seed):
+def test_mixed_solve_parity(solver, prec, refine, M, N, gap, seed):
     H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -gap / 2), (gap / 2, 1.0), seed=seed)
     ref = o.solve(H, N, tol=1e-12)
-    D, info = solver.solve(_dev(H), N, prec=prec, tol=1e-10)
+    D, info = solver.solve(_dev(H), N, prec=prec, tol=1e-10, refine=refine)
     Dg = D.cpu().numpy()
     assert info["status"] == 0, info
     assert info["idem_fro"] <= 1e-10
+    # the device residual is the refinement's own; recheck it in plain FP64
+    assert np.linalg.norm(Dg @ Dg - Dg) <= 2e-10
     assert abs(np.trace(Dg) - N) <= 1e-9
     dmax = np.abs(Dg - ref["D"]).max()
     dfro = np.linalg.norm(Dg - ref["D"]) / np.sqrt(N)
@@ -92,7 +95,8 @@ def test_split_only_reaches_its_floor(solver):
 def test_mixed_history_phases(solver):
     M, N = 384, 96
     H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.05), (0.05, 1.0), seed=13)
-    D, info = solver.solve(_dev(H), N, prec="mixed_fp16", tol=1e-11, history_cap=300)
+    D, info = solver.solve(_dev(H), N, prec="mixed_fp16", tol=1e-11, history_cap=300,
+                           refine="fp64")
     hist = solver.history(300)
     phases = [int(h["phase"]) for h in hist]
     assert phases[0] == 1 and phases[-1] == 0
@@ -112,3 +116,18 @@ def test_mixed_with_float32_hamiltonian(solver):
     assert info["status"] == 0
     assert abs(info["energy"] - ref["E"]) / M <= 1e-10
     assert np.abs(D.cpu().numpy() - ref["D"]).max() <= 3e-6
+
+
+def test_slice_refinement_agrees_with_fp64_refinement(solver):
+    """Both refinements purify the same split-phase result: the exact-slice
+    McWeeny steps and the FP64 HPCP steps land on the same projector."""
+    M, N = 1000, 250
+    H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -0.02), (0.02, 1.0), seed=21)
+    Ds, i_s = solver.solve(_dev(H), N, prec="mixed_fp16", tol=1e-10, refine="slices")
+    Df, i_f = solver.solve(_dev(H), N, prec="mixed_fp16", tol=1e-10, refine="fp64")
+    assert i_s["status"] == 0 and i_f["status"] == 0
+    assert i_s["iters_lowp"] == i_f["iters_lowp"]
+    a, b = Ds.cpu().numpy(), Df.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-9
+    assert abs(np.trace(a) - N) <= 1e-9
+    assert abs(i_s["energy"] - i_f["energy"]) <= 1e-12 * abs(i_f["energy"])
