@@ -119,6 +119,30 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def lookup_traffic(kernel, M):
+    """DRAM bytes per launch of `kernel` at this M from the committed ncu
+    summary table, or None when there is none or the kernel's source file
+    changed since the capture (its SHA-256 is recorded beside the figure)."""
+    import hashlib
+    table = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if kernel is None or not os.path.exists(table):
+        return None
+    for line in open(table):
+        f = line.split()
+        if len(f) != 5 or line.startswith("#"):
+            continue
+        name, m, src, sha, nbytes = f
+        if name != kernel or int(m) != M:
+            continue
+        path = os.path.join(ROOT, "paper_1512_07236_gb300", "csrc", src)
+        if not os.path.exists(path):
+            return None
+        if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
+            return None
+        return float(nbytes)
+    return None
+
+
 def oracle_sample(H, N, iters):
     """The FP64 oracle as it stands, `iters` purification steps of the
     workload; returns (seconds, applied steps)."""
@@ -228,9 +252,13 @@ def main():
         }
         del Dref, diff, Qo
 
-    # --- dominant kernel: tensor-core GEMMs, timed alone with CUDA events --
+    # --- the products, each timed alone with CUDA events ------------------
+    # Per launch, algorithmic work = one dense-equivalent product, 2 M^3.
+    # Executed tensor work counts the computed 128 x 256 upper tiles: 3
+    # products for a split GEMM, 54 digit-slice pairs for the exact D^2 (the
+    # 53 pairs of weights 0..9 of nine slices plus the (5, 5) square), 3 for
+    # the refinement's (D^2 - D) D.
     split_prec = "bf16x3" if "bf16" in args.prec else "fp16x3"
-    roof = None
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -239,24 +267,46 @@ def main():
         pass
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     fp16_note = "of measured" if "bf16_tflops" in peaks else "of fallback"
+    Mp = ((M + 255) // 256) * 256
+    ntiles = sum(min(2 * j + 2, Mp // 128) for j in range(Mp // 256))
+    tile_flops = 2.0 * ntiles * 128 * 256 * Mp
+    alg = 2.0 * M ** 3
+    lp, l64 = infos[-1]["iters_lowp"], infos[-1]["iters_fp64"]
+    kern = {}
     try:
         solver.solve(Ht, N, out=D, **opts)
-        t1, t2 = solver.time_kernels(M, N, prec=split_prec, reps=5)
-        alg = 2.0 * M ** 3  # dense-equivalent flops of one product
-        achieved = 2 * alg / ((t1 + t2) * 1e-3) / 1e12
-        # executed tensor flops: 3 products over the computed upper tiles
-        Mp = ((M + 255) // 256) * 256
-        ntiles = sum(min(2 * j + 2, Mp // 128) for j in range(Mp // 256))
-        executed = 3 * 2.0 * ntiles * 128 * 256 * Mp
-        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": achieved / bf16_peak, "traffic": None,
-                "kernel": "tc_gemm_kernel (GEMM1 + GEMM2 of one step)",
-                "ms_gemm1": t1, "ms_gemm2": t2,
-                "executed_tflops": 2 * executed / ((t1 + t2) * 1e-3) / 1e12,
-                "peak_note": f"bf16 dense burst {fp16_note} (fp16 has the same nominal rate)"}
+        if "mixed" in args.prec or args.prec in ("fp16x3", "bf16x3"):
+            t1, t2 = solver.time_kernels(M, N, prec=split_prec, reps=5)
+            kern["tc_gemm_kernel"] = {
+                "what": "split GEMM1 + GEMM2 of one step", "ms": [t1, t2], "launches_per_solve": 2 * lp,
+                "ms_per_solve": (t1 + t2) * lp, "achieved_tflops": 2 * alg / ((t1 + t2) * 1e-3) / 1e12,
+                "executed_tflops": 2 * 3 * tile_flops / ((t1 + t2) * 1e-3) / 1e12}
+        if "mixed" in args.prec and l64 > 0:
+            o1, o2 = solver.time_kernels(M, N, prec=args.prec, reps=3)
+            kern["oz_gemm_kernel"] = {
+                "what": "exact digit-slice D^2 of one refinement step", "ms": o1,
+                "launches_per_solve": l64, "ms_per_solve": o1 * l64,
+                "achieved_tflops": alg / (o1 * 1e-3) / 1e12,
+                "executed_tflops": 54 * tile_flops / (o1 * 1e-3) / 1e12}
+            kern["tc_gemm_kernel<3>"] = {
+                "what": "refinement product (D^2 - D) D", "ms": o2, "launches_per_solve": l64,
+                "ms_per_solve": o2 * l64, "executed_tflops": 3 * tile_flops / (o2 * 1e-3) / 1e12}
     except Exception as e:  # noqa: BLE001
-        roof = {"bound": "tensor", "achieved": None, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "error": str(e)}
+        kern["error"] = str(e)
+    roof = {"bound": "tensor", "achieved": None, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": None, "traffic": None}
+    timed = {k: v for k, v in kern.items() if isinstance(v, dict)}
+    if timed:
+        top = max(timed, key=lambda k: timed[k]["ms_per_solve"])
+        kt = timed[top]
+        ach = kt.get("achieved_tflops", kt["executed_tflops"])
+        roof.update({"achieved": ach, "frac": ach / bf16_peak, "kernel": top,
+                     "executed_tflops": kt["executed_tflops"],
+                     "executed_frac": kt["executed_tflops"] / bf16_peak,
+                     "share_of_solve": kt["ms_per_solve"] / ms_step,
+                     "peak_note": f"bf16 dense burst {fp16_note} (fp16 has the same nominal "
+                                  "rate); achieved = 2 M^3 per launch / mean launch time"})
+    roof["traffic"] = lookup_traffic(top if timed else None, M)
 
     # --- plain FP64 GPU path: time to the same tolerance -------------------
     fp64 = None
@@ -296,11 +346,20 @@ def main():
                "sample": f"{n} FP64 purification steps of M={M} (numpy + host BLAS), "
                          f"{t:.1f} s"}
 
-    # kernel launches per solve: guess 4, per WHILE body 6 (two steps),
-    # transition 2, copy-out 1, energy 2
-    lp, l64 = infos[-1]["iters_lowp"], infos[-1]["iters_fp64"]
-    bodies = (lp + 2) // 2 + ((l64 + 2) // 2 if "mixed" in args.prec or args.prec == "fp64" else 0)
-    launches = args.steps * (4 + 6 * bodies + 2 + 1 + 2)
+    # kernel launches per solve: guess 4; each WHILE body holds two steps and
+    # runs (evaluations + 1) // 2 times, evaluations = applied steps + 1;
+    # split step 3 launches (GEMM1, control, GEMM2), FP64 step 3, slice
+    # refinement step 5 (slice, slice GEMM, finalize, control, product);
+    # phase change 2; copy-out 1; energy 2
+    split_phase = "mixed" in args.prec or args.prec in ("fp16x3", "bf16x3")
+    f64_phase = "mixed" in args.prec or args.prec == "fp64"
+    ref_step = 5 if ("mixed" in args.prec and "oz_gemm_kernel" in kern) else 3
+    per_solve = 4 + 1 + 2
+    if split_phase:
+        per_solve += 6 * ((lp + 2) // 2)
+    if f64_phase:
+        per_solve += 2 * ref_step * ((l64 + 2) // 2) + (2 if "mixed" in args.prec else 0)
+    launches = args.steps * per_solve
 
     if rank == 0:
         line = {
@@ -320,6 +379,7 @@ def main():
             "speedup_vs_fp64_gpu": (fp64["ms"] / ms_step) if fp64 else None,
             "accuracy": acc,
             "roofline": roof,
+            "kernels": kern,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s",
                     "h2d_bytes_per_step": M * M * 8, "d2h_bytes_per_step": M * M * 8},

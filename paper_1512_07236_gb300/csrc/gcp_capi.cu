@@ -1098,13 +1098,18 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
     gcp_default_options(&o);
   cudaStream_t s = (cudaStream_t)o.stream;
   const bool split = prec == GCP_FP16X3 || prec == GCP_BF16X3;
+  const bool refine = prec == GCP_MIXED_FP16 || prec == GCP_MIXED_BF16;
   if (split) {
     if (h->mp != tc_pad(M) || h->tc_bf16 != (prec == GCP_BF16X3) || !h->opS)
       return fail(h, GCP_ERR_NO_CHECKPOINT, "gcp_time_kernels: no split workspace of this size");
+  } else if (refine) {
+    if (h->oz_mp != tc_pad(M) || !h->oz_op || h->m64 < M)
+      return fail(h, GCP_ERR_NO_CHECKPOINT,
+                  "gcp_time_kernels: no slice-refinement workspace of this size");
   } else if (prec == GCP_FP64) {
     if (h->m64 < M) return fail(h, GCP_ERR_NO_CHECKPOINT, "gcp_time_kernels: no FP64 workspace");
   } else {
-    return fail(h, GCP_ERR_INVALID_ARG, "gcp_time_kernels: prec must be FP64, FP16X3 or BF16X3");
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_time_kernels: bad prec");
   }
   // a live state: apply = 1 with c = 1/2 (McWeeny coefficients)
   State init;
@@ -1121,7 +1126,10 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   const int Mp = h->mp, bf = h->tc_bf16;
   CK(cudaEventRecord(e[0], s));
   for (int r = 0; r < reps; ++r) {
-    if (split) {
+    if (refine) {
+      if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, h->oz_mp, h->st, s))
+        return fail(h, GCP_ERR_CUDA, "slice GEMM launch failed");
+    } else if (split) {
       if (tc_launch_gemm1(h->opX[0], h->X[0], h->Sig, h->Sh, h->Sl, M, Mp, nullptr, 1, M, h->part,
                           h->st, bf, kSplitScale, nullptr, s))
         return fail(h, GCP_ERR_CUDA, "GEMM1 launch failed");
@@ -1132,7 +1140,11 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   CK(cudaEventRecord(e[1], s));
   CK(cudaEventRecord(e[2], s));
   for (int r = 0; r < reps; ++r) {
-    if (split) {
+    if (refine) {
+      if (tc_launch_mcweeny64(h->oz_opX, h->oz_opD, h->S64, h->D64[0], h->D64[1], h->oz_xscale,
+                              h->oz_rscale, M, h->oz_mp, h->st, s))
+        return fail(h, GCP_ERR_CUDA, "refinement product launch failed");
+    } else if (split) {
       if (tc_launch_gemm2(h->opS, h->opX[0], h->X[0], h->Sig, h->X[1], h->Xh[1], h->Xl[1], M, Mp,
                           h->st, bf, kSplitScale, nullptr, s))
         return fail(h, GCP_ERR_CUDA, "GEMM2 launch failed");

@@ -4,7 +4,7 @@
 // takes ~0.45 s.  Here D^2 is formed on the tensor cores without rounding:
 //   * each row i of D is scaled by 2^e_i with |D_ij| <= 2^e_i / 2 and cut
 //     into nine signed base-32 digits, D_ij = 2^e_i sum_s d_s 32^-(s+1) + r,
-//     |d_s| <= 16, |r| <= 2^e_i 32^-9 / 2 (a 46-bit fixed-point value);
+//     |d_s| <= 16, |r| <= 2^e_i 32^-9 / 2 (a 45-bit fixed-point value);
 //     digits are small integers, exact in fp16;
 //   * (D D)_ij = 2^(e_i+e_j) sum_w 32^-(w+2) sum_{s+t=w} sum_k d_s(i,k) d_t(j,k)
 //     for weights w = 0..9; the dropped weights (w >= 10) and the cut r each
@@ -82,6 +82,11 @@ __device__ __forceinline__ void oz_tile(int t, int NI, int NJ, int& I, int& J) {
 }
 
 // ---- slicing ---------------------------------------------------------------
+// GB300 issues FP64 at a small fraction of its integer rate, so the digits
+// come from integer arithmetic: one exact power-of-two scaling and rounding
+// gives the 45-bit fixed-point value n = rint(2^45 D_ij / 2^e_i), |n| <= 2^44,
+// and its balanced base-32 digits follow by rounding shifts, most
+// significant first, each remainder exact.
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ D, int M, int Mp,
                                                        const OzSlicePtrs slices,
                                                        double* __restrict__ rscale,
@@ -89,44 +94,55 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
                                                        __half* __restrict__ Dl,
                                                        const State* __restrict__ st) {
   if (st->stopped) return;
-  __shared__ double red[32];
-  __shared__ double scale_sh;
+  __shared__ unsigned long long red[32];
+  __shared__ int e_sh;
   const int i = blockIdx.x;
-  double mx = 0.0;
+  // row max of |D_ij| as the largest magnitude bit pattern (monotone for
+  // non-negative doubles)
+  unsigned long long mb = 0ull;
   if (i < M)
-    for (int j = threadIdx.x; j < M; j += blockDim.x) mx = fmax(mx, fabs(D[(size_t)i * M + j]));
-  // block max
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong(D[(size_t)i * M + j]) & 0x7fffffffffffffffull;
+      mb = b > mb ? b : mb;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = t > mb ? t : mb;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    // smallest power of two with m <= 2^e / 2
+    unsigned long long b = 0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = red[w] > b ? red[w] : b;
+    const double m = __longlong_as_double((long long)b);
+    // smallest power of two with m <= 2^e / 2 (rows below 2^-900 are cut to 0)
     int e = 0;
     if (m > 0.0) {
       frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
       e += 1;
     }
-    scale_sh = ldexp(1.0, e);
-    rscale[i] = scale_sh;
+    e = e < -900 ? -900 : e;
+    e_sh = e;
+    rscale[i] = ldexp(1.0, e);
   }
   __syncthreads();
-  const double inv = 1.0 / scale_sh;  // exact: a power of two
+  const double to_fixed = ldexp(1.0, 45 - e_sh);  // exact: a power of two
   for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
     const double d = (i < M && j < M) ? D[(size_t)i * M + j] : 0.0;
-    double v = d * inv;  // |v| <= 1/2
-    // fp16 halves of 2^14 v (|.| <= 2^13) for the refinement product
-    const double vs = v * kRefScale;
-    const __half h = __double2half(vs);
-    Dh[(size_t)i * Mp + j] = h;
-    Dl[(size_t)i * Mp + j] = __double2half(vs - (double)__half2float(h));
+    long long n = __double2ll_rn(d * to_fixed);
+    const size_t o = (size_t)i * Mp + j;
+    // fp16 halves of 2^14 D_ij / 2^e_i = n 2^-31 (|.| <= 2^13), ~22 bits
+    const float f = (float)n * 0x1p-31f;
+    const __half h = __float2half_rn(f);
+    Dh[o] = h;
+    Dl[o] = __float2half_rn(f - __half2float(h));
 #pragma unroll
     for (int s = 0; s < kOzSlices; ++s) {
-      const double t = v * 32.0;
-      const double dg = rint(t);  // |dg| <= 16
-      v = t - dg;                 // exact
-      slices.p[s][(size_t)i * Mp + j] = __double2half((float)dg);
+      const int k = 5 * (kOzSlices - 1 - s);
+      const long long dg = k > 0 ? ((n + (1ll << (k > 0 ? k - 1 : 0))) >> k) : n;  // |dg| <= 16
+      n -= dg << k;  // exact, |n| <= 2^(k-1)
+      slices.p[s][o] = __int2half_rn((int)dg);
     }
   }
 }

@@ -16,9 +16,11 @@
 // Accumulation.  The tensor cores add into their FP32 accumulator with
 // truncation; over a long K that biases every sum toward zero (measured
 // ~6e-5 relative at K = 8192 for same-sign sums).  So the accumulator only
-// ever holds one K chunk of 64 (12 MMAs): eight drain warps move each chunk
-// from TMEM into FP32 registers with round-to-nearest adds while the MMA
-// warp fills the other of two TMEM buffers.
+// ever holds one K chunk of 128 (24 MMAs; 32 in the refinement product):
+// eight drain warps move each chunk from TMEM into FP32 registers with
+// round-to-nearest adds while the MMA warp fills the other of two TMEM
+// buffers.  (Chunks of 64 cost 16% more
+// time in GEMM1 at M = 8192 for no measurable gain in accuracy.)
 //
 // GEMM1 (Y = X X).  With S = D^2 = theta^2 J + Sigma, Sigma = 2 theta X + Y,
 // the epilogue writes Sigma (FP32 + halves, exactly symmetric) and per-tile
@@ -57,7 +59,15 @@ struct TcOperands {
 namespace {
 using namespace tcx;
 constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
-constexpr int KC_STAGES = 2;  // K chunk per TMEM drain = KC_STAGES * BK = 64
+// K chunk per TMEM drain = kc_stages * BK: 128 for the split phase; 32 for
+// the FP64 refinement product (mode 3), whose trace must hold to ~1e-10:
+// the truncation inside a chunk biases the diagonal of (S - D) D toward
+// zero by about (MMAs per chunk) 2^-25, and 24 MMAs per chunk moved
+// Tr D_{n+1} by ~1e-9 at M = 8192.
+template <int MODE>
+__host__ __device__ constexpr int kc_stages() {
+  return MODE == 3 ? 1 : 4;
+}
 constexpr int kThreads = 320;
 constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
         TileCtx c;
         make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
-        const int nchunk = c.nkb / KC_STAGES;
+        const int nchunk = c.nkb / kc_stages<MODE>();
         for (int ch = 0; ch < nchunk && alive; ++ch, ++qc) {
           const uint32_t b = qc & 1;
           if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
@@ -412,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t acc = tmem + b * 256;
-          for (int ks = 0; ks < KC_STAGES; ++ks, ++g) {
+          for (int ks = 0; ks < kc_stages<MODE>(); ++ks, ++g) {
             const uint32_t s = g % STAGES;
             if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
               atomicOr(timeout_flag, 1);
@@ -455,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float acc[128];
 #pragma unroll
       for (int k = 0; k < 128; ++k) acc[k] = 0.f;
-      const int nchunk = c.nkb / KC_STAGES;
+      const int nchunk = c.nkb / kc_stages<MODE>();
       for (int ch = 0; ch < nchunk; ++ch, ++qc) {
         const uint32_t b = qc & 1;
         if (alive) {

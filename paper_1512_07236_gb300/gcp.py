@@ -266,8 +266,11 @@ class Solver:
         return out
 
     def time_kernels(self, M, N, prec="fp16x3", reps=10):
-        """Mean duration (ms) of GEMM1 and GEMM2 of one step, CUDA events on
-        the current stream; needs a prior solve of size M on this handle."""
+        """Mean duration (ms) of the two products of one step, CUDA events on
+        the current stream; needs a prior solve of size M on this handle.
+        prec "fp16x3"/"bf16x3": GEMM1 and GEMM2 of a split step; "fp64": the
+        FP64 products; "mixed_fp16"/"mixed_bf16": the digit-slice D^2 and the
+        (D^2 - D) D product of an exact-slice refinement step."""
         ms = (C.c_double * 2)()
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         o = make_options()
