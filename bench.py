@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=2)
     p.add_argument("--no-graph", action="store_true",
                    help="host-driven loop (same kernels, one launch each; for launch lists)")
+    p.add_argument("--workload", default="dense", choices=["dense", "tb", "batched", "adjoint"],
+                   help="dense: the headline (one dense H); tb: tight-binding 20^3 insulator; "
+                        "batched: 512 uneven instances; adjoint: dL/dH through 40 steps")
     return p.parse_args()
 
 
@@ -184,11 +187,139 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _cuda_ms(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, out
+
+
+def run_workload(args, rank):
+    """The other workloads of the method, one JSON line each (rank 0)."""
+    import numpy as np
+    import torch
+
+    from paper_1512_07236_gb300 import gcp, inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    solver = gcp.Solver()
+    W, K = max(args.warmup, 1), max(args.steps, 1)
+    line = {"n_gpus": 1, "steps": K, "warmup": W, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    if args.workload == "tb":
+        Hf = inputs.tight_binding_cubic(L=20, seed=3)
+        M, N = Hf.shape[0], Hf.shape[0] // 2
+        Ht = torch.from_numpy(Hf).cuda()
+        D = torch.empty((M, M), dtype=torch.float64, device="cuda")
+        opts = dict(prec=args.prec, tol=TOL)
+        for _ in range(W):
+            solver.solve(Ht, N, out=D, **opts)
+        with ClockSampler(0) as clk:
+            ms, (_, info) = _cuda_ms(lambda: solver.solve(Ht, N, out=D, **opts), K, stream)
+        H64 = Ht.double()
+        lam = torch.linalg.eigvalsh(H64)
+        E_ref = float(lam[:N].sum())
+        R = float(torch.linalg.norm(D @ D - D))
+        fp64_ms = None
+        if not args.skip_fp64:
+            fp64_ms, (_, i64) = _cuda_ms(lambda: solver.solve(Ht, N, prec="fp64", tol=TOL), 1,
+                                         stream)
+        line.update({
+            "metric": "time to ||D^2-D||_F<=1e-6, tight-binding insulator", "value": ms * 1e-3,
+            "unit": "s", "higher_is_better": False, "ms_per_step": ms, "dtype": "fp16x3+f64",
+            "config": {"workload": "simple-cubic 20^3 tight-binding, t=-1, onsite +-0.5, "
+                                   "disorder 0.1, FP32 storage, N=4000", "M": M, "N": N,
+                       "prec": args.prec, "iters": info["iters"]},
+            "energy_err_per_site": abs(info["energy"] - E_ref) / M,
+            "idem_fro": R, "trace_err": abs(float(torch.trace(D)) - N),
+            "fp64_gpu_path_ms": fp64_ms,
+            "speedup_vs_fp64_gpu": fp64_ms / ms if fp64_ms else None,
+            "clocks": clk.summary()})
+    elif args.workload == "batched":
+        items = inputs.batched_rotated(512, qr_backend="torch")
+        Hs = [torch.from_numpy(H).cuda() for H, _, _, _ in items]
+        Ns = [N for _, N, _, _ in items]
+        opts = dict(prec=args.prec, tol=TOL)
+        for _ in range(W):
+            solver.solve_batched(Hs, Ns, **opts)
+        with ClockSampler(0) as clk:
+            ms, (Ds, infos) = _cuda_ms(lambda: solver.solve_batched(Hs, Ns, **opts), K, stream)
+        single = gcp.Solver()
+        for H, N in zip(Hs[:4], Ns[:4]):
+            single.solve(H, N, **opts)
+        loop_ms, _ = _cuda_ms(lambda: [single.solve(H, N, **opts) for H, N in zip(Hs, Ns)], 1,
+                              stream)
+        errs = []
+        for (H, N, eps, Q), Dk in zip(items[:32], Ds[:32]):
+            Qo = torch.from_numpy(Q[:, :N]).cuda()
+            errs.append(float(torch.linalg.norm(Dk - Qo @ Qo.T)) / np.sqrt(N))
+        flops = sum(4.0 * H.shape[0] ** 3 * i["iters"] for H, i in zip(Hs, infos))
+        line.update({
+            "metric": "batched solves/s to ||D^2-D||_F<=1e-6", "value": 512 / (ms * 1e-3),
+            "unit": "solves/s", "higher_is_better": True, "ms_per_step": ms,
+            "dtype": "fp16x3+f64" if "mixed" in args.prec else args.prec,
+            "config": {"workload": "512 rotated spectra, M in {64,96,...,1024}, N=M/4, "
+                                   "gap U[0.02,0.2]", "prec": args.prec,
+                       "sum_M2": int(sum(H.shape[0] ** 2 for H in Hs))},
+            "loop_of_single_solves_per_s": 512 / (loop_ms * 1e-3),
+            "speedup_vs_loop": loop_ms / ms,
+            "effective_tflops": flops / (ms * 1e-3) / 1e12,
+            "status_ok": sum(1 for i in infos if i["status"] == 0),
+            "max_subspace_err_first32": max(errs), "clocks": clk.summary()})
+    else:  # adjoint
+        M, N, Kst = 2048, 512, 40
+        H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -0.025), (0.025, 1.0), seed=5,
+                                            qr_backend="torch")
+        V = inputs.symmetric_gaussian(M, 0.1, seed=6)
+        Ht, Vt = torch.from_numpy(H).cuda(), torch.from_numpy(V).cuda()
+        g = torch.empty_like(Ht)
+        run = lambda: solver.backward(Ht, N, Kst, G_D=Vt, g_E=1.0, ckpt_every=8, out=g)
+        for _ in range(W):
+            run()
+        with ClockSampler(0) as clk:
+            ms, _ = _cuda_ms(run, K, stream)
+        fwd_ms, _ = _cuda_ms(lambda: solver.solve(Ht, N, prec="fp64", fixed_iters=Kst), 1,
+                             stream)
+        gH = g.cpu().numpy()
+
+        def loss(Hx):
+            D, info = solver.solve(torch.from_numpy(Hx).cuda(), N, prec="fp64",
+                                   fixed_iters=Kst)
+            return float((D * Vt).sum()) + info["energy"]
+
+        rng = np.random.default_rng(8)
+        rel = []
+        for _ in range(4):
+            Ed = rng.standard_normal((M, M))
+            Ed = Ed + Ed.T
+            Ed /= np.linalg.norm(Ed)
+            fd = (loss(H + 1e-4 * Ed) - loss(H - 1e-4 * Ed)) / 2e-4
+            rel.append(abs(float(np.sum(gH * Ed)) - fd) / max(abs(fd), 1e-30))
+        line.update({
+            "metric": "dL/dH through 40 GCP steps (forward + adjoint)", "value": ms * 1e-3,
+            "unit": "s", "higher_is_better": False, "ms_per_step": ms, "dtype": "f64",
+            "config": {"workload": "M=2048 N=512 gap 0.05, L = Tr(DH) + Tr(DV), V ~ N(0,0.01)",
+                       "fixed_iters": Kst, "ckpt_every": 8},
+            "forward_only_ms": fwd_ms, "fd_rel_err_max": max(rel), "clocks": clk.summary()})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "dense":
+        run_workload(args, rank)
         return
     import numpy as np
     import torch
