@@ -15,6 +15,11 @@ Functions and the passages they follow:
 
 * ``gershgorin_bounds``      Gershgorin disc bounds used in Eq. pmcpguess.
 * ``canonical_guess``        Eq. dmguess with the coefficients of Eq. pmcpguess.
+* ``hole_guess``             the hole guess (beta_1 = thetabar,
+                             beta_2 = -max{...}) before Eq. hpcpguess.
+* ``hpcp_plus_guess``        Eq. hpcpguess with the alpha search of
+                             Eq. hpcpguessalpha.
+* ``solve_holes``            hole purification (Eq. hpcp3 on Dbar).
 * ``coefficient_c``          Eq. mcwgamb (c_n, the PM unstable fixed point).
 * ``gamma_from_c``           Eq. mcwgama with d = 0.
 * ``hpcp_step``              Eq. hpcp3 (closed-form hole-particle step).
@@ -38,8 +43,11 @@ specification, not by code):
 1. c_n uses the computed Tr D_n, not N; the step then conserves the
    trace for any value of c (Eqs. mcwgamb, hpcp1a).
 2. Two stop tests are offered: ||D^2 - D||_F <= tol (computed elementwise)
-   and Tr(D Dbar) <= tol (the paper's test).
-3. 0/0 guard: when den = Tr(D - D^2) <= den_min with
+   and |Tr(D Dbar)| <= tol (the paper's test; Tr(D Dbar) >= 0 while the
+   spectrum of D lies in [0, 1], but the hole and mixed guesses of
+   Eq. hpcpguess can start outside it, where a negative Tr(D Dbar) is not
+   convergence).
+3. 0/0 guard: when |den| = |Tr(D - D^2)| <= den_min with
    den_min = 16 * M * u * max(1, Tr D) (u = 2^-53) and the stop test still
    fails, the step uses c = 1/2 (the McWeeny step of Eq. mcweeny3, which the
    recursion reaches as gamma -> 0): c itself would be rounding noise over
@@ -52,6 +60,11 @@ specification, not by code):
    point.
 6. Test Eq. testb is read as ||D||_F^2 - N (= Tr D^2 - N).
 7. E = Tr(H D) without a spin factor.
+8. Eq. hpcpguessalpha (garbled case conditions): delta = 2/3; the target
+   Tr(D+_0^2) = N - delta N applies for theta <= 1 - delta, the target
+   N - delta Nbar for theta >= delta (each has a real solution only there),
+   and alpha = 1/2 (the paper's naive value, good for 0.3 < theta < 0.7) in
+   between.
 """
 from __future__ import annotations
 
@@ -110,6 +123,70 @@ def canonical_guess(H, N):
     D0 = theta * np.eye(M) + beta2 * (mu * np.eye(M) - H)
     return D0, dict(mu=mu, theta=theta, beta1=theta, beta2=beta2, hmin=hmin, hmax=hmax,
                     no_gap=no_gap)
+
+
+def hole_guess(H, N):
+    """Initial hole density matrix Dbar_0 = beta_1 I + beta_2 (mu I - H) with
+    beta_1 = thetabar and beta_2 = -max(theta/(H_max - mu),
+    thetabar/(mu - H_min))   (Eqs. dmguess and pmcpguess for the hole
+    matrix, in the text before Eq. hpcpguess).  Returns (Dbar0, info)."""
+    H = np.asarray(H, dtype=np.float64)
+    M = H.shape[0]
+    _, info = canonical_guess(H, N)
+    theta = info["theta"]
+    mu = info["mu"]
+    bt = theta / (info["hmax"] - mu)
+    bb = (1.0 - theta) / (mu - info["hmin"])
+    bmax = max(bt, bb)
+    Dbar0 = (1.0 - theta) * np.eye(M) - bmax * (mu * np.eye(M) - H)
+    return Dbar0, dict(info, beta1_hole=1.0 - theta, beta2_hole=-bmax, beta_max=bmax,
+                       beta_min=min(bt, bb))
+
+
+def hpcp_plus_guess(H, N, delta=2.0 / 3.0, alpha=None):
+    """Mixed guess D+_0 = alpha D_0 + (1 - alpha)(I - Dbar_0)   (Eq. hpcpguess).
+
+    Without ``alpha``, alpha is searched in [0, 1] so that Tr(D+_0^2) equals
+    N - delta N when theta <= 1 - delta, or N - delta Nbar when theta >= delta
+    (Eq. hpcpguessalpha; Nbar = M - N), and alpha = 1/2 in between.  As the
+    paper does it: Tr((alpha A + (1 - alpha) B)^2) with A = D_0,
+    B = I - Dbar_0 is the quadratic
+      alpha^2 Tr(A^2) + 2 alpha (1 - alpha) Tr(AB) + (1 - alpha)^2 Tr(B^2)
+    in alpha (one extra product, A B), solved with numpy.roots; its root in
+    [0, 1] is taken (the trace is monotone in alpha there), else the end of
+    [0, 1] nearer to the target.  Returns (D0, info) with alpha."""
+    H = np.asarray(H, dtype=np.float64)
+    M = H.shape[0]
+    A, info = canonical_guess(H, N)
+    if info["no_gap"]:
+        return A, dict(info, alpha=1.0)
+    Dbar0, hinfo = hole_guess(H, N)
+    B = np.eye(M) - Dbar0
+    theta = info["theta"]
+    if alpha is None:
+        if theta <= 1.0 - delta:
+            target = N - delta * N
+        elif theta >= delta:
+            target = N - delta * (M - N)
+        else:
+            target = None
+        if target is None:
+            alpha = 0.5
+        else:
+            tAA = float(np.trace(A @ A))
+            tBB = float(np.trace(B @ B))
+            tAB = float(np.trace(A @ B))
+            coef = [tAA - 2.0 * tAB + tBB, 2.0 * tAB - 2.0 * tBB, tBB - target]
+            roots = [r.real for r in np.roots(coef) if abs(r.imag) < 1e-12]
+            inside = [r for r in roots if -1e-12 <= r <= 1.0 + 1e-12]
+            if inside:
+                alpha = min(max(inside[0], 0.0), 1.0)
+            else:
+                # Tr at alpha = 0 (largest spread) vs the target
+                alpha = 0.0 if target >= tBB else 1.0
+    D0 = alpha * A + (1.0 - alpha) * B
+    return D0, dict(info, alpha=float(alpha), beta2=alpha * info["beta2"]
+                    + (1.0 - alpha) * hinfo["beta_max"], beta_max=hinfo["beta_max"])
 
 
 # ----------------------------------------------------------------------------
@@ -182,8 +259,14 @@ def pm_dual_constrained_step(D, c):
 # The recursion with termination
 # ----------------------------------------------------------------------------
 def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None,
-          record=True):
+          record=True, guess="canonical", method="hpcp"):
     """Purify the canonical guess of H with the recursion of Eq. hpcp3.
+
+    ``guess``: "canonical" (Eq. dmguess / Eq. pmcpguess), "hpcp+"
+    (Eq. hpcpguess with the search of Eq. hpcpguessalpha) or "hole"
+    (I - Dbar_0: the particle iterate of hole purification, see
+    ``solve_holes``).  ``method``: "hpcp" (Eq. hpcp3) or "pmcp" (the
+    Palser-Manolopoulos step of Eq. pm1 with the same c_n).
 
     Per iteration n (all in float64):
       S  = D D
@@ -207,7 +290,14 @@ def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None
         return dict(D=D, E=float(np.sum(D * H)), iters=0, status=STATUS_OK, history=[],
                     guess=None)
     if D0 is None:
-        D, info = canonical_guess(H, N)
+        if guess == "canonical":
+            D, info = canonical_guess(H, N)
+        elif guess == "hpcp+":
+            D, info = hpcp_plus_guess(H, N)
+        elif guess == "hole":
+            D, info = hpcp_plus_guess(H, N, alpha=0.0)
+        else:
+            raise ValueError("unknown guess")
     else:
         D, info = np.array(D0, dtype=np.float64), None
     if info is not None and info["no_gap"]:
@@ -232,7 +322,7 @@ def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None
                 status = STATUS_OK
                 break
         else:
-            crit = R if stop == "idem_fro" else den
+            crit = R if stop == "idem_fro" else abs(den)
             if crit <= tol:
                 hist.append(rec)
                 status = STATUS_OK
@@ -246,7 +336,7 @@ def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None
                 status = STATUS_NOT_CONVERGED
                 break
         den_min = 16.0 * M * U_FP64 * max(1.0, T1)
-        if den <= den_min:
+        if abs(den) <= den_min:
             if fixed_iters > 0:
                 hist.append(rec)
                 n += 1
@@ -263,10 +353,30 @@ def solve(H, N, tol=1e-12, stop="idem_fro", max_iter=100, fixed_iters=0, D0=None
             status = STATUS_ILL_CONDITIONED
             break
         P = S @ D
-        D = (1.0 - 2.0 * c) * D + (2.0 + 2.0 * c) * S - 2.0 * P
+        if method == "pmcp":
+            if c <= 0.5:
+                D = ((1.0 - 2.0 * c) * D + (1.0 + c) * S - P) / (1.0 - c)
+            else:
+                D = ((1.0 + c) * S - P) / c
+        else:
+            D = (1.0 - 2.0 * c) * D + (2.0 + 2.0 * c) * S - 2.0 * P
         R_prev = [R, R_prev[0]]
         n += 1
     return dict(D=D, E=float(np.sum(D * H)), iters=n, status=status, history=hist, guess=info)
+
+
+def solve_holes(H, N, **kw):
+    """Hole purification: Eq. hpcp3 applied to Dbar from the hole guess
+    (text before Eq. hpcpguess), N_bar = M - N holes; returns the particle
+    result D = I - Dbar_inf (Eq. closure) in the same dict layout as solve."""
+    H = np.asarray(H, dtype=np.float64)
+    M = H.shape[0]
+    if N == 0 or N == M:
+        return solve(H, N, **kw)
+    Dbar0, info = hole_guess(H, N)
+    r = solve(H, M - N, D0=Dbar0, **kw)
+    D = np.eye(M) - r["D"]
+    return dict(r, D=D, E=float(np.sum(D * H)), guess=info)
 
 
 def energy(D, H):
