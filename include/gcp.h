@@ -100,7 +100,43 @@ typedef struct {
                           gcp_solve only);  1 FP64 SIMT products and HPCP
                           steps (always used otherwise, and by
                           gcp_solve_batched) */
+  int guess;           /* gcp_guess (default GCP_GUESS_CANONICAL) */
+  int method;          /* gcp_method (default GCP_METHOD_HPCP) */
 } gcp_options;
+
+/* Initial guess.
+ *   GCP_GUESS_CANONICAL  Eq. dmguess with the coefficients of Eq. pmcpguess:
+ *                        D0 = theta I + beta_min (mu I - H).
+ *   GCP_GUESS_HPCP_PLUS  Eq. hpcpguess, D0 = alpha D0_canonical +
+ *                        (1 - alpha)(I - Dbar0) with the hole guess
+ *                        Dbar0 = thetabar I - beta_max (mu I - H); alpha in
+ *                        [0, 1] from Eq. hpcpguessalpha with delta = 2/3:
+ *                        Tr D0^2 = N - delta N if theta <= 1/3,
+ *                        N - delta (M - N) if theta >= 2/3, alpha = 1/2
+ *                        otherwise.  Equivalently D0 = theta I + b (mu I - H),
+ *                        b = alpha beta_min + (1 - alpha) beta_max.
+ *   GCP_GUESS_HOLE       I - Dbar0 (alpha = 0): purifying it is the hole
+ *                        purification of the paper (Eq. hpcp3 on Dbar), by
+ *                        the particle-hole duality of the recursion.  Its
+ *                        spectrum leaves [0, 1] away from half filling,
+ *                        where the solve reports GCP_ERR_ILL_CONDITIONED.
+ * gcp_solve_batched and gcp_backward take GCP_GUESS_CANONICAL only. */
+typedef enum {
+  GCP_GUESS_CANONICAL = 0,
+  GCP_GUESS_HPCP_PLUS = 1,
+  GCP_GUESS_HOLE = 2
+} gcp_guess;
+
+/* Recursion.
+ *   GCP_METHOD_HPCP  Eq. hpcp3: D+ = (1-2c) D + (2+2c) D^2 - 2 D^3.
+ *   GCP_METHOD_PMCP  the canonical purification of Appendix A, Eq. pm1:
+ *                    c <= 1/2: D+ = [(1-2c) D + (1+c) D^2 - D^3] / (1-c),
+ *                    c >  1/2: D+ = [(1+c) D^2 - D^3] / c,
+ *                    same c_n (Eq. mcwgamb).
+ * Both conserve Tr D.  The refinement steps of the mixed modes are the
+ * McWeeny step with the trace-restoring c for either method.  gcp_backward
+ * differentiates GCP_METHOD_HPCP only. */
+typedef enum { GCP_METHOD_HPCP = 0, GCP_METHOD_PMCP = 1 } gcp_method;
 
 typedef struct {
   int status;        /* gcp_status of the solve */
@@ -112,7 +148,9 @@ typedef struct {
   double idem_fro;   /* ||D^2 - D||_F at the last evaluated iterate */
   double trace_ddbar;/* Tr(D - D^2) at the last evaluated iterate */
   double c_last;     /* last c_n used */
-  double mu, beta2, hmin, hmax; /* guess parameters (Eq. pmcpguess) */
+  double mu, beta2, hmin, hmax; /* guess parameters (Eq. pmcpguess); beta2 is
+                                   the coefficient b actually used */
+  double alpha;      /* mixing coefficient of Eq. hpcpguess (1 = canonical) */
 } gcp_result;
 
 /* Per-step record written when history_cap > 0 (gcp_get_history):

@@ -351,7 +351,8 @@ int adjoint_backward(void** wsp, const void* H, int M, int N, int ld, int h_f64,
 
   // ---------------- forward with checkpoints -----------------------------
   launch_guess_reduce(H, h_f64, M, ld, gpart, s);
-  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, st, s);
+  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld,
+                        GCP_GUESS_CANONICAL, st, s);
   launch_state_init(st, 0, s);
   launch_guess_write_d(H, h_f64, M, ld, D64_0, 1, M, M, st, s);
   AD_CK(cudaPeekAtLastError());
@@ -407,7 +408,7 @@ int adjoint_backward(void** wsp, const void* H, int M, int N, int ld, int h_f64,
                                                       M, G);
   const int T = (M + kBT - 1) / kBT;
   const int nfull = T * T, nup = T * (T + 1) / 2;
-  State rs;  // replay state for the recomputation (apply, a, b)
+  State rs;  // replay state for the recomputation (apply, a, b, g3)
   memset(&rs, 0, sizeof rs);
   for (int seg = (K - 1) / ck; seg >= 0; --seg) {
     const int n0 = seg * ck, n1 = (n0 + ck < K) ? n0 + ck : K;
@@ -421,6 +422,7 @@ int adjoint_backward(void** wsp, const void* H, int M, int N, int ld, int h_f64,
       rs.apply = applied ? 1 : 0;
       rs.a = applied ? 1.0 - 2.0 * c : 1.0;
       rs.b = applied ? 2.0 + 2.0 * c : 0.0;
+      rs.g3 = -2.0;  // HPCP (Eq. hpcp3)
       AD_CK(cudaMemcpyAsync(st, &rs, sizeof rs, cudaMemcpyHostToDevice, s));
       launch_f64_gemm1(segD + (size_t)j * m2, segS + (size_t)j * m2, M, M, nullptr, 1, M, part, st,
                        s);
@@ -456,7 +458,8 @@ int adjoint_backward(void** wsp, const void* H, int M, int N, int ld, int h_f64,
   // ---------------- guess ------------------------------------------------
   // restore the guess parameters (the replay state overwrote the state)
   launch_guess_reduce(H, h_f64, M, ld, gpart, s);
-  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, st, s);
+  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld,
+                        GCP_GUESS_CANONICAL, st, s);
   if (h_f64) {
     adj_gersh_kernel<double><<<kRedBlocks, 256, 0, s>>>((const double*)H, ld, M, rpart);
     adj_gersh_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc);

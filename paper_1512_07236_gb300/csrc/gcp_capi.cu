@@ -149,7 +149,7 @@ gcp_status ensure_common(Handle* h, size_t ntiles, int M, int hist_cap) {
     CK(grow(&h->part, h->part_n, ntiles * kPartFields));
     h->part_n = ntiles * kPartFields;
   }
-  const size_t gp = (size_t)guess_partial_blocks(M) * 4;
+  const size_t gp = (size_t)guess_partial_blocks(M) * kGuessFields;
   if (gp > h->gpart_n) {
     drop_graph(h);
     CK(grow(&h->gpart, h->gpart_n, gp));
@@ -272,6 +272,7 @@ Ctl make_ctl(const SolveArgs& a, int phase, int final_phase) {
   c.final_phase = final_phase;
   c.tol = a.o.tol;
   c.u = phase == 1 ? kU32 : kU64;
+  c.method = a.o.method;
   return c;
 }
 
@@ -370,7 +371,8 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
   const int M = a.M, N = a.N;
   const bool split = is_split(a.o.prec), mixed = is_mixed(a.o.prec);
   launch_guess_reduce(a.H, a.h_f64, M, a.ld, h->gpart, s);
-  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, h->st, s);
+  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, a.H, a.h_f64, a.ld, a.o.guess,
+                        h->st, s);
   launch_state_init(h->st, split ? 1 : 0, s);
   if (split) {
     launch_guess_write_x(a.H, a.h_f64, M, a.ld, h->X[0], h->Xh[0], h->Xl[0], h->mp, h->tc_bf16,
@@ -456,11 +458,17 @@ void fill_result(const State& hs, gcp_result* res) {
   res->c_last = hs.c;
   res->mu = hs.mu;
   res->beta2 = hs.beta2;
+  res->alpha = hs.alpha;
   res->hmin = hs.hmin;
   res->hmax = hs.hmax;
 }
 
 bool valid_dtype(int d) { return d == GCP_F64 || d == GCP_F32; }
+
+bool valid_modes(const gcp_options& o) {
+  return o.guess >= GCP_GUESS_CANONICAL && o.guess <= GCP_GUESS_HOLE &&
+         (o.method == GCP_METHOD_HPCP || o.method == GCP_METHOD_PMCP);
+}
 
 }  // namespace
 
@@ -550,11 +558,13 @@ gcp_status gcp_init_guess(void* hv, const void* H, int M, int N, int ld, int h_d
     o = *opt;
   else
     gcp_default_options(&o);
+  if (!valid_modes(o)) return fail(h, GCP_ERR_INVALID_ARG, "gcp_init_guess: bad guess or method");
   cudaStream_t s = (cudaStream_t)o.stream;
   gcp_status r = ensure_common(h, 1, M, 0);
   if (r != GCP_OK) return r;
   launch_guess_reduce(H, h_dtype == GCP_F64, M, ld, h->gpart, s);
-  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, h->st, s);
+  launch_guess_finalize(h->gpart, guess_partial_blocks(M), M, N, H, h_dtype == GCP_F64, ld,
+                        o.guess, h->st, s);
   launch_guess_write_d(H, h_dtype == GCP_F64, M, ld, D0, d_dtype == GCP_F64, ldd, M, h->st, s);
   CK(cudaPeekAtLastError());
   State hs;
@@ -580,7 +590,7 @@ gcp_status gcp_step(void* hv, void* D, int M, int N, int ld, int d_dtype, double
   else
     gcp_default_options(&o);
   if (!D || M <= 0 || N < 0 || N > M || ld < M || !valid_dtype(d_dtype) || o.prec < 0 ||
-      o.prec > GCP_MIXED_BF16)
+      o.prec > GCP_MIXED_BF16 || !valid_modes(o))
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_step: bad arguments");
   cudaStream_t s = (cudaStream_t)o.stream;
   SolveArgs a{};
@@ -645,7 +655,7 @@ gcp_status gcp_solve(void* hv, const void* H, int M, int N, int ld, int h_dtype,
     gcp_default_options(&o);
   if (!H || !D_out || M <= 0 || N < 0 || N > M || ld < M || ldd < M || !valid_dtype(h_dtype) ||
       !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
-      o.history_cap < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1))
+      o.history_cap < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || !valid_modes(o))
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve: bad arguments");
   cudaStream_t s = (cudaStream_t)o.stream;
   if (res) memset(res, 0, sizeof *res);
@@ -750,6 +760,9 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
       !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || o.history_cap != 0)
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad arguments");
+  if (!valid_modes(o)) return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad guess or method");
+  if (o.guess != GCP_GUESS_CANONICAL)
+    return fail(h, GCP_ERR_UNSUPPORTED, "gcp_solve_batched: canonical guess only");
   for (int b = 0; b < batch; ++b)
     if (!H[b] || !D_out[b] || M[b] <= 0 || N[b] < 0 || N[b] > M[b] || ld[b] < M[b])
       return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad instance %d", b);
@@ -828,7 +841,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   off += al(sizeof(double) * kPartFields * (size_t)(ntc > nf64 ? ntc : nf64));
   const size_t gpart_off = off;
   const int gstride = guess_partial_blocks(maxM);
-  off += al(sizeof(double) * 4 * (size_t)gstride * (size_t)nb);
+  off += al(sizeof(double) * kGuessFields * (size_t)gstride * (size_t)nb);
   const size_t active_off = off;
   off += al(sizeof(int));
   if (off > h->arena_bytes) {
@@ -1073,6 +1086,9 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
                 "gcp_backward: bad arguments (needs 0 < N < M and opt->fixed_iters > 0)");
   if (o.prec != GCP_FP64)
     return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: the adjoint runs in FP64 (prec = GCP_FP64)");
+  if (o.guess != GCP_GUESS_CANONICAL || o.method != GCP_METHOD_HPCP)
+    return fail(h, GCP_ERR_UNSUPPORTED,
+                "gcp_backward: differentiates the canonical guess and HPCP steps only");
   cudaStream_t s = (cudaStream_t)o.stream;
   gcp_status r;
   if ((r = ensure_common(h, f64_num_tiles(M), M, o.fixed_iters + 2)) != GCP_OK) return r;
@@ -1119,6 +1135,7 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   init.c = 0.5;
   init.a = 0.0;
   init.b = 3.0;
+  init.g3 = -2.0;
   init.xshift = 2.0 * init.theta * (1.0 - init.theta) * (init.theta - 0.5);
   CK(cudaMemcpyAsync(h->st, &init, sizeof init, cudaMemcpyHostToDevice, s));
   cudaEvent_t e[4];

@@ -23,6 +23,40 @@ constexpr int kCtlThreads = 256;
 
 // One control decision from the summed partials v of the iterate's GEMM1.
 // Returns 1 when the phase stops for this state (already stopped included).
+// Coefficients of D+ = a D + b S + g3 S D for c and the method, and the J
+// coefficient of the shifted update X+ = D+ - theta J (split phase):
+//   HPCP (Eq. hpcp3): a = 1 - 2c, b = 2 + 2c, g3 = -2,
+//     xshift = 2 theta (1 - theta)(theta - c);
+//   PMCP (Eq. pm1): c <= 1/2: a = (1-2c)/(1-c), b = (1+c)/(1-c), g3 = -1/(1-c);
+//     c > 1/2: a = 0, b = (1+c)/c, g3 = -1/c;
+//     xshift = a theta + b theta^2 + g3 theta^3 - theta.
+// Both give the McWeeny step (Eq. mcweeny3) at c = 1/2.
+__device__ void set_coeffs(State* st, double c, int method) {
+  const double th = st->theta;
+  st->c = c;
+  if (method == GCP_METHOD_PMCP) {
+    double a, b, g3;
+    if (c <= 0.5) {
+      a = (1.0 - 2.0 * c) / (1.0 - c);
+      b = (1.0 + c) / (1.0 - c);
+      g3 = -1.0 / (1.0 - c);
+    } else {
+      a = 0.0;
+      b = (1.0 + c) / c;
+      g3 = -1.0 / c;
+    }
+    st->a = a;
+    st->b = b;
+    st->g3 = g3;
+    st->xshift = a * th + b * th * th + g3 * th * th * th - th;
+  } else {
+    st->a = 1.0 - 2.0 * c;
+    st->b = 2.0 + 2.0 * c;
+    st->g3 = -2.0;
+    st->xshift = 2.0 * th * (1.0 - th) * (th - c);
+  }
+}
+
 __device__ int control_decide(const double (&v)[5], State* st, double* hist, const Ctl& ctl) {
   if (st->stopped) return 1;
   // FP64 phase: v = (Tr D, Tr S, sum S o D, R^2, E).
@@ -83,7 +117,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       kind = 1;
     }
   } else {
-    const double crit = (ctl.stop == GCP_STOP_IDEMP_FRO) ? R : den;
+    const double crit = (ctl.stop == GCP_STOP_IDEMP_FRO) ? R : fabs(den);
     if (crit <= ctl.tol) {
       stop = 1;
       kind = 1;
@@ -132,7 +166,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       const double g = ((double)ctl.N - (3.0 * T2 - 2.0 * T3)) / den;
       if (fabs(g) <= 0.1) c_mcw = 0.5 * (1.0 - g);
     }
-    if (den <= den_min && !mcw) {
+    if (fabs(den) <= den_min && !mcw) {
       if (ctl.fixed_iters > 0) {
         st->apply = 0;  // identity step
         st->n = n + 1;
@@ -147,11 +181,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
         // FP64, Tr(D - D^2) at rounding level but R > tol: McWeeny step
         // (c = 1/2), as in the oracle; the stagnation rule ends a loop that
         // can go no further
-        st->c = 0.5;
-        st->a = 0.0;
-        st->b = 3.0;
-        const double th = st->theta;
-        st->xshift = 2.0 * th * (1.0 - th) * (th - 0.5);
+        set_coeffs(st, 0.5, GCP_METHOD_HPCP);
         st->apply = 1;
         st->Rp1 = st->Rp0;
         st->Rp0 = R;
@@ -161,23 +191,32 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       }
     } else {
       // Split phase (before the endgame): c also absorbs the FP32 rounding
-      // drift of the trace, c = (num + (Tr D - N)/2) / den, so that
-      // Tr D_{n+1} = N for the traces as computed (exact arithmetic gives
-      // Tr D_n = N and the plain Eq. mcwgamb).  FP64: Eq. mcwgamb.
-      const double c = mcw ? c_mcw
-                           : (ctl.phase == 1 ? (num + 0.5 * (T1 - (double)ctl.N)) / den
-                                             : num / den);
+      // drift of the trace, so that Tr D_{n+1} = N for the traces as
+      // computed (exact arithmetic gives Tr D_n = N and the plain
+      // Eq. mcwgamb): with delta = Tr D - N, HPCP takes
+      // c = (num + delta/2) / den; PMCP (Eq. pm1) c = (num + delta)/(den +
+      // delta) on its c <= 1/2 branch and num / (den - delta) on the other.
+      // FP64: Eq. mcwgamb.
+      double c;
+      if (mcw) {
+        c = c_mcw;
+      } else if (ctl.phase == 1) {
+        const double dl = T1 - (double)ctl.N;
+        if (ctl.method == GCP_METHOD_PMCP)
+          c = (num / den <= 0.5) ? (num + dl) / (den + dl) : num / (den - dl);
+        else
+          c = (num + 0.5 * dl) / den;
+      } else {
+        c = num / den;
+      }
+      const int method = mcw ? (int)GCP_METHOD_HPCP : ctl.method;
       if (n == 0 && !(c >= 0.0 && c <= 1.0) && ctl.fixed_iters == 0) {
         stop = 1;
         kind = 3;
         status = GCP_ERR_ILL_CONDITIONED;
       } else if (ctl.endgame && n > 0 && !(c >= -0.05 && c <= 1.05) && ctl.fixed_iters == 0) {
         // c left the stable domain (rounding noise): McWeeny step instead
-        st->c = 0.5;
-        st->a = 0.0;
-        st->b = 3.0;
-        const double th = st->theta;
-        st->xshift = 2.0 * th * (1.0 - th) * (th - 0.5);
+        set_coeffs(st, 0.5, GCP_METHOD_HPCP);
         st->apply = 1;
         st->Rp1 = st->Rp0;
         st->Rp0 = R;
@@ -186,11 +225,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
         st->parity ^= 1;
         if (rec) rec[5] = 0.5;
       } else {
-        st->c = c;
-        st->a = 1.0 - 2.0 * c;
-        st->b = 2.0 + 2.0 * c;
-        const double th = st->theta;
-        st->xshift = 2.0 * th * (1.0 - th) * (th - c);
+        set_coeffs(st, c, method);
         st->apply = 1;
         st->Rp1 = st->Rp0;
         st->Rp0 = R;
@@ -313,6 +348,7 @@ __device__ void state_init_dev(State* st, int phase) {
   }
   st->c = __longlong_as_double(0x7ff8000000000000ll);
   st->a = st->b = 0.0;
+  st->g3 = -2.0;
   st->T1 = st->T2 = st->T3 = st->R = st->E = 0.0;
   st->Rp0 = st->Rp1 = INFINITY;
   st->xshift = 0.0;

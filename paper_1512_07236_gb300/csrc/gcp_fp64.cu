@@ -17,8 +17,9 @@
 // over the upper triangle, with w = 2 above the diagonal (the element
 // stands for its mirror) and 1 on it.  One record of partials per tile; the control kernel sums
 // them in tile order, so the result does not depend on scheduling.
-// GEMM2 (P = S D) epilogue: D_{n+1} = a D + b S - 2 P with a = 1 - 2c,
-// b = 2 + 2c (Eq. hpcp3 expanded).
+// GEMM2 (P = S D) epilogue: D_{n+1} = a D + b S + g3 P with the step's
+// coefficients from the state (HPCP, Eq. hpcp3 expanded: a = 1 - 2c,
+// b = 2 + 2c, g3 = -2; PMCP: Eq. pm1).
 #include "gcp_device.cuh"
 #include "gcp_fp64_tile.cuh"
 #include "gcp_internal.cuh"
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) f64_gemm2_kernel(const double* __res
   const int m0 = bi * BT, n0 = bj * BT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool apply = st->apply != 0;
-  const double a = st->a, b = st->b;
+  const double a = st->a, b = st->b, g3 = st->g3;
   double acc[RT][RT];
   if (apply) {
     f64_mainloop<BT>(S, D, M, ld, m0, n0, acc, As, Bs);
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) f64_gemm2_kernel(const double* __res
       if (r < M && c < M && c >= r) {
         const size_t o = (size_t)r * ld + c;
         const double d = D[o];
-        const double x = apply ? (a * d + b * S[o] - 2.0 * acc[i][j]) : d;
+        const double x = apply ? (a * d + b * S[o] + g3 * acc[i][j]) : d;
         Dn[o] = x;
         if (c != r) Dn[(size_t)c * ld + r] = x;
       }
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) batch_f64_gemm2_kernel(const BatchIt
   const int m0 = bi * kBT, n0 = bj * kBT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool apply = st->apply != 0;
-  const double a = st->a, b = st->b;
+  const double a = st->a, b = st->b, g3 = st->g3;
   double acc[RT][RT];
   if (apply) f64_mainloop<kBT>(S, D, M, ld, m0, n0, acc, As, Bs);
 #pragma unroll
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) batch_f64_gemm2_kernel(const BatchIt
       if (r < M && c < M && c >= r) {
         const size_t o = (size_t)r * ld + c;
         const double d = D[o];
-        const double x = apply ? (a * d + b * S[o] - 2.0 * acc[i][j]) : d;
+        const double x = apply ? (a * d + b * S[o] + g3 * acc[i][j]) : d;
         Dn[o] = x;
         if (c != r) Dn[(size_t)c * ld + r] = x;
       }

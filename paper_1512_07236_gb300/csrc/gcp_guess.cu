@@ -1,13 +1,26 @@
-// Canonical initial guess (Eq. dmguess with the coefficients of Eq. pmcpguess).
+// Initial guess: the canonical guess (Eq. dmguess with the coefficients of
+// Eq. pmcpguess), the mixed HPCP+ guess (Eq. hpcpguess, alpha from
+// Eq. hpcpguessalpha) and the hole guess I - Dbar0.  All three are
+//   D0 = theta I + b (mu I - H)
+// with b = beta_min (canonical), b = beta_max (hole: I - Dbar0 with
+// Dbar0 = thetabar I - beta_max (mu I - H)), or
+// b = alpha beta_min + (1 - alpha) beta_max (HPCP+), where
+// beta_min / beta_max are the smaller / larger of theta/(H_max - mu) and
+// thetabar/(mu - H_min).
 //
 // Pass 1 (HBM-bound, one read of H): per row i the Gershgorin disc
 //   [H_ii - r_i, H_ii + r_i], r_i = sum_{j != i} |H_ij|,
-// reduced to H_min = min_i(H_ii - r_i), H_max = max_i(H_ii + r_i), Tr H and
-// max|H_ii|; one warp per row, per-block partials (deterministic order).
-// Pass 2 (one block): mu = Tr H / M, theta = N/M,
-//   beta2 = min{theta/(H_max - mu), (1-theta)/(mu - H_min)}.
+// reduced to H_min = min_i(H_ii - r_i), H_max = max_i(H_ii + r_i), Tr H,
+// max|H_ii| and sum_{j != i} H_ij^2; one warp per row, per-block partials
+// (deterministic order).
+// Pass 2 (one block): mu = Tr H / M, theta = N/M, the betas and b.  For
+// HPCP+, Tr D0^2 = M theta^2 + b^2 F with F = ||mu I - H||_F^2 (the trace of
+// mu I - H vanishes), so the target of Eq. hpcpguessalpha fixes
+// b^2 = (target - M theta^2) / F and alpha = (beta_max - b)/(beta_max -
+// beta_min), clamped to [0, 1]; F is the off-diagonal sum of pass 1 plus
+// sum_i (H_ii - mu)^2 read from the diagonal.
 // Pass 3 (HBM-bound, read H once, write D0 once):
-//   D0 = theta I + beta2 (mu I - H), or the shifted X0 = D0 - theta J with
+//   D0 = theta I + b (mu I - H), or the shifted X0 = D0 - theta J with
 //   its split halves for the tensor-core path.
 #include "gcp_device.cuh"
 #include "gcp_internal.cuh"
@@ -18,79 +31,152 @@ namespace {
 constexpr int kGuessThreads = 256;
 constexpr int kGuessMaxBlocks = 1216;  // 8 x 152 SMs
 
+// Per-row Gershgorin terms accumulated by one warp (lanes end identical).
+template <typename T>
+__device__ __forceinline__ void guess_row(const T* __restrict__ row, int i, int M, double& lo,
+                                          double& hi, double& tr, double& mx, double& off2) {
+  const int lane = threadIdx.x & 31;
+  double r = 0.0, q = 0.0;
+  for (int j = lane; j < M; j += 32) {
+    const double h = (double)row[j];
+    r += fabs(h);
+    q += h * h;
+  }
+  r = warp_sum(r);
+  q = warp_sum(q);
+  const double d = (double)row[i];
+  r -= fabs(d);
+  lo = fmin(lo, d - r);
+  hi = fmax(hi, d + r);
+  tr += d;
+  mx = fmax(mx, fabs(d));
+  off2 += q - d * d;
+}
+
+// Combine the warps of a block in a fixed order into part[0..4].
+__device__ __forceinline__ void guess_block_combine(double lo, double hi, double tr, double mx,
+                                                    double off2, double* sh,
+                                                    double* __restrict__ part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[warp * kGuessFields + 0] = lo;
+    sh[warp * kGuessFields + 1] = hi;
+    sh[warp * kGuessFields + 2] = tr;
+    sh[warp * kGuessFields + 3] = mx;
+    sh[warp * kGuessFields + 4] = off2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = INFINITY, b = -INFINITY, t = 0.0, m = 0.0, o = 0.0;
+    for (int w = 0; w < kGuessThreads / 32; ++w) {
+      a = fmin(a, sh[w * kGuessFields + 0]);
+      b = fmax(b, sh[w * kGuessFields + 1]);
+      t += sh[w * kGuessFields + 2];
+      m = fmax(m, sh[w * kGuessFields + 3]);
+      o += sh[w * kGuessFields + 4];
+    }
+    part[0] = a;
+    part[1] = b;
+    part[2] = t;
+    part[3] = m;
+    part[4] = o;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGuessThreads) guess_reduce_kernel(const T* __restrict__ H,
                                                                       int M, int ld,
                                                                       double* __restrict__ part) {
-  __shared__ double sh[32 * 4];
-  const int lane = threadIdx.x & 31;
+  __shared__ double sh[32 * kGuessFields];
   const int warps_per_block = kGuessThreads / 32;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;
-  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0;
-  for (int i = gw; i < M; i += nw) {
-    const T* row = H + (size_t)i * ld;
-    double r = 0.0;
-    for (int j = lane; j < M; j += 32) r += fabs((double)row[j]);
-    r = warp_sum(r);
-    const double d = (double)row[i];
-    r -= fabs(d);
-    lo = fmin(lo, d - r);
-    hi = fmax(hi, d + r);
-    tr += d;  // identical in every lane
-    mx = fmax(mx, fabs(d));
-  }
-  // lanes hold identical values; combine warps in a fixed order
-  const int warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[warp * 4 + 0] = lo;
-    sh[warp * 4 + 1] = hi;
-    sh[warp * 4 + 2] = tr;
-    sh[warp * 4 + 3] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = INFINITY, b = -INFINITY, t = 0.0, m = 0.0;
-    for (int w = 0; w < warps_per_block; ++w) {
-      a = fmin(a, sh[w * 4 + 0]);
-      b = fmax(b, sh[w * 4 + 1]);
-      t += sh[w * 4 + 2];
-      m = fmax(m, sh[w * 4 + 3]);
-    }
-    part[blockIdx.x * 4 + 0] = a;
-    part[blockIdx.x * 4 + 1] = b;
-    part[blockIdx.x * 4 + 2] = t;
-    part[blockIdx.x * 4 + 3] = m;
-  }
+  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0, off2 = 0.0;
+  for (int i = gw; i < M; i += nw) guess_row(H + (size_t)i * ld, i, M, lo, hi, tr, mx, off2);
+  guess_block_combine(lo, hi, tr, mx, off2, sh, part + (size_t)blockIdx.x * kGuessFields);
 }
 
-__global__ void guess_finalize_kernel(const double* __restrict__ part, int nblocks, int M, int N,
-                                      State* st) {
-  if (threadIdx.x != 0) return;
-  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    lo = fmin(lo, part[b * 4 + 0]);
-    hi = fmax(hi, part[b * 4 + 1]);
-    tr += part[b * 4 + 2];
-    mx = fmax(mx, part[b * 4 + 3]);
-  }
+// Guess coefficients into the state from the combined partials.
+__device__ void guess_params(double lo, double hi, double tr, double mx, double F, int M, int N,
+                             int mode, State* st) {
   const double theta = (double)N / (double)M;
   const double mu = tr / (double)M;
   // zero-width interval (H = mu I up to rounding): beta2 undefined
   const int no_gap = (hi - lo) <= 8.0 * (double)M * kU64 * fmax(1.0, mx);
-  double beta2 = 0.0;
+  double b = 0.0, alpha = 1.0;
   if (!no_gap) {
     double bt = INFINITY, bb = INFINITY;
     if (hi - mu > 0.0) bt = theta / (hi - mu);
     if (mu - lo > 0.0) bb = (1.0 - theta) / (mu - lo);
-    beta2 = fmin(bt, bb);
+    const double bmin = fmin(bt, bb), bmax = fmax(bt, bb);
+    b = bmin;
+    if (mode != GCP_GUESS_CANONICAL && isfinite(bmax)) {
+      if (mode == GCP_GUESS_HOLE) {
+        alpha = 0.0;
+      } else {
+        const double delta = 2.0 / 3.0, Md = (double)M, Nd = (double)N;
+        double target = 0.0;
+        bool has = true;
+        if (theta <= 1.0 - delta)
+          target = Nd - delta * Nd;
+        else if (theta >= delta)
+          target = Nd - delta * (Md - Nd);
+        else
+          has = false;
+        alpha = 0.5;
+        if (has && F > 0.0 && bmax > bmin) {
+          const double b2 = (target - Md * theta * theta) / F;
+          const double bt2 = b2 > 0.0 ? sqrt(b2) : 0.0;
+          alpha = fmin(fmax((bmax - bt2) / (bmax - bmin), 0.0), 1.0);
+        }
+      }
+      b = alpha * bmin + (1.0 - alpha) * bmax;
+    }
   }
   st->mu = mu;
-  st->beta2 = beta2;
+  st->beta2 = b;
+  st->alpha = alpha;
   st->hmin = lo;
   st->hmax = hi;
   st->theta = theta;
   st->no_gap = no_gap;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGuessThreads) guess_finalize_kernel(
+    const double* __restrict__ part, int nblocks, int M, int N, const T* __restrict__ H, int ld,
+    int mode, State* st) {
+  __shared__ double red[32];
+  __shared__ double mu_sh;
+  __shared__ double acc[kGuessFields];
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0, off2 = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      const double* p = part + (size_t)b * kGuessFields;
+      lo = fmin(lo, p[0]);
+      hi = fmax(hi, p[1]);
+      tr += p[2];
+      mx = fmax(mx, p[3]);
+      off2 += p[4];
+    }
+    acc[0] = lo;
+    acc[1] = hi;
+    acc[2] = tr;
+    acc[3] = mx;
+    acc[4] = off2;
+    mu_sh = tr / (double)M;
+  }
+  __syncthreads();
+  double v[1] = {0.0};
+  if (mode == GCP_GUESS_HPCP_PLUS) {
+    const double mu = mu_sh;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const double d = (double)H[(size_t)i * ld + i] - mu;
+      v[0] += d * d;
+    }
+  }
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) guess_params(acc[0], acc[1], acc[2], acc[3], acc[4] + v[0], M, N, mode, st);
 }
 
 template <typename T, typename O>
@@ -146,9 +232,14 @@ void launch_guess_reduce(const void* H, int h_f64, int M, int ld, double* part, 
     guess_reduce_kernel<float><<<nb, kGuessThreads, 0, s>>>((const float*)H, M, ld, part);
 }
 
-void launch_guess_finalize(const double* part, int nblocks, int M, int N, State* st,
-                           cudaStream_t s) {
-  guess_finalize_kernel<<<1, 32, 0, s>>>(part, nblocks, M, N, st);
+void launch_guess_finalize(const double* part, int nblocks, int M, int N, const void* H,
+                           int h_f64, int ld, int guess_mode, State* st, cudaStream_t s) {
+  if (h_f64)
+    guess_finalize_kernel<double><<<1, kGuessThreads, 0, s>>>(part, nblocks, M, N,
+                                                             (const double*)H, ld, guess_mode, st);
+  else
+    guess_finalize_kernel<float><<<1, kGuessThreads, 0, s>>>(part, nblocks, M, N,
+                                                            (const float*)H, ld, guess_mode, st);
 }
 
 void launch_guess_write_d(const void* H, int h_f64, int M, int ld, void* D, int d_f64, int ldd,
@@ -198,50 +289,18 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(kGuessThreads) batch_guess_reduce_kernel(
     const BatchItem* items, double* __restrict__ gpart) {
-  __shared__ double sh[32 * 4];
+  __shared__ double sh[32 * kGuessFields];
   const BatchItem& it = items[blockIdx.y];
   if ((int)blockIdx.x >= it.gblocks) return;  // this instance uses gblocks blocks
   const T* H = (const T*)it.H;
   const int M = it.M, ld = it.ld;
-  const int lane = threadIdx.x & 31;
   const int warps_per_block = kGuessThreads / 32;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = it.gblocks * warps_per_block;
-  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0;
-  for (int i = gw; i < M; i += nw) {
-    const T* row = H + (size_t)i * ld;
-    double r = 0.0;
-    for (int j = lane; j < M; j += 32) r += fabs((double)row[j]);
-    r = warp_sum(r);
-    const double d = (double)row[i];
-    r -= fabs(d);
-    lo = fmin(lo, d - r);
-    hi = fmax(hi, d + r);
-    tr += d;
-    mx = fmax(mx, fabs(d));
-  }
-  const int warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[warp * 4 + 0] = lo;
-    sh[warp * 4 + 1] = hi;
-    sh[warp * 4 + 2] = tr;
-    sh[warp * 4 + 3] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = INFINITY, b = -INFINITY, t = 0.0, m = 0.0;
-    for (int w = 0; w < warps_per_block; ++w) {
-      a = fmin(a, sh[w * 4 + 0]);
-      b = fmax(b, sh[w * 4 + 1]);
-      t += sh[w * 4 + 2];
-      m = fmax(m, sh[w * 4 + 3]);
-    }
-    double* p = gpart + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4;
-    p[0] = a;
-    p[1] = b;
-    p[2] = t;
-    p[3] = m;
-  }
+  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0, off2 = 0.0;
+  for (int i = gw; i < M; i += nw) guess_row(H + (size_t)i * ld, i, M, lo, hi, tr, mx, off2);
+  guess_block_combine(lo, hi, tr, mx, off2, sh,
+                      gpart + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kGuessFields);
 }
 
 __global__ void batch_guess_finalize_kernel(const BatchItem* items, int batch,
@@ -249,32 +308,15 @@ __global__ void batch_guess_finalize_kernel(const BatchItem* items, int batch,
   const int bi = blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= batch) return;
   const BatchItem& it = items[bi];
-  State* st = it.st;
   double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0;
   for (int k = 0; k < it.gblocks; ++k) {
-    const double* p = gpart + ((size_t)bi * gstride + k) * 4;
+    const double* p = gpart + ((size_t)bi * gstride + k) * kGuessFields;
     lo = fmin(lo, p[0]);
     hi = fmax(hi, p[1]);
     tr += p[2];
     mx = fmax(mx, p[3]);
   }
-  const int M = it.M, N = it.N;
-  const double theta = (double)N / (double)M;
-  const double mu = tr / (double)M;
-  const int no_gap = (hi - lo) <= 8.0 * (double)M * kU64 * fmax(1.0, mx);
-  double beta2 = 0.0;
-  if (!no_gap) {
-    double bt = INFINITY, bb = INFINITY;
-    if (hi - mu > 0.0) bt = theta / (hi - mu);
-    if (mu - lo > 0.0) bb = (1.0 - theta) / (mu - lo);
-    beta2 = fmin(bt, bb);
-  }
-  st->mu = mu;
-  st->beta2 = beta2;
-  st->hmin = lo;
-  st->hmax = hi;
-  st->theta = theta;
-  st->no_gap = no_gap;
+  guess_params(lo, hi, tr, mx, 0.0, it.M, it.N, GCP_GUESS_CANONICAL, it.st);
 }
 
 template <typename T, bool BF16>

@@ -31,6 +31,8 @@ struct State {
   double Rp0, Rp1;          // residuals of the two previous evaluated iterates
   double mu, beta2, hmin, hmax, theta;
   double xshift;            // J coefficient of X+ (split phase)
+  double g3;                // D^3 coefficient of the step (-2 for HPCP)
+  double alpha;             // mixing coefficient of the guess (Eq. hpcpguess)
 };
 
 // Scalar options every control kernel needs (passed by value).
@@ -44,6 +46,7 @@ struct Ctl {
   int final_phase;  // this phase decides the final status
   int endgame;      // McWeeny endgame (split and refinement phases only)
   int mcw_only;     // every step is a McWeeny step (exact-slice refinement)
+  int method;       // gcp_method
   double tol;
   double u;         // unit roundoff of the phase's state (den guard)
 };
@@ -78,11 +81,14 @@ struct BatchItem {
 
 // ---- guess (gcp_guess.cu) ------------------------------------------------
 int guess_partial_blocks(int M);
-// Gershgorin row bounds, trace, max|H_ii|: per-block partials (4 doubles).
+// Per-block partials of the guess reduction: min_i(H_ii - r_i),
+// max_i(H_ii + r_i), Tr H, max|H_ii|, sum_{i != j} H_ij^2.
+constexpr int kGuessFields = 5;
 void launch_guess_reduce(const void* H, int h_f64, int M, int ld, double* part, cudaStream_t s);
-// Combine partials, compute mu, beta2, write into State.
-void launch_guess_finalize(const double* part, int nblocks, int M, int N, State* st,
-                           cudaStream_t s);
+// Combine partials into mu, theta and the coefficient b of the guess
+// (gcp_guess mode; the HPCP+ search reads the diagonal of H), into State.
+void launch_guess_finalize(const double* part, int nblocks, int M, int N, const void* H,
+                           int h_f64, int ld, int guess_mode, State* st, cudaStream_t s);
 // D0 = theta I + beta2 (mu I - H) (FP64 or FP32 out), padded area zero.
 void launch_guess_write_d(const void* H, int h_f64, int M, int ld, void* D, int d_f64, int ldd,
                           int rows_pad, const State* st, cudaStream_t s);
@@ -96,7 +102,7 @@ int f64_num_tiles(int M);
 // S = D D over upper tiles, mirrored; epilogue partials per tile.
 void launch_f64_gemm1(const double* D, double* S, int M, int ld, const void* H, int h_f64, int ldh,
                       double* part, const State* st, cudaStream_t s);
-// Dn = a D + b S - 2 S D over upper tiles, mirrored.
+// Dn = a D + b S + g3 S D over upper tiles, mirrored (a, b, g3 from State).
 void launch_f64_gemm2(const double* S, const double* D, double* Dn, int M, int ld,
                       const State* st, cudaStream_t s);
 

@@ -39,7 +39,7 @@ constexpr size_t kMat = (size_t)kNoAllocMaxM * kNoAllocMaxM;
 // per-tile partials of the FP64 GEMM1 at the largest size, and the
 // per-block partials of the guess and energy reductions
 constexpr size_t kPartN = 256 * kPartFields;
-constexpr size_t kGpartN = 256;
+constexpr size_t kGpartN = 512;
 constexpr size_t kStateN = (sizeof(State) + sizeof(double) - 1) / sizeof(double);
 constexpr size_t kScratchDoubles = 3 * kMat + kPartN + kGpartN + kStateN + 32;
 
@@ -100,7 +100,9 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
   }
   if (!H || !D_out || M <= 0 || N < 0 || N > M || ld < M || ldd < M ||
       (h_dtype != GCP_F64 && h_dtype != GCP_F32) || (d_dtype != GCP_F64 && d_dtype != GCP_F32) ||
-      o.max_iter < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1)) {
+      o.max_iter < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) ||
+      o.guess < GCP_GUESS_CANONICAL || o.guess > GCP_GUESS_HOLE ||
+      (o.method != GCP_METHOD_HPCP && o.method != GCP_METHOD_PMCP)) {
     set_err(err, errlen, "gcp_solve_noalloc: bad arguments");
     return GCP_ERR_INVALID_ARG;
   }
@@ -109,7 +111,7 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
     return GCP_ERR_UNSUPPORTED;
   }
   if ((size_t)f64_num_tiles(M) * kPartFields > kPartN ||
-      (size_t)guess_partial_blocks(M) * 4 > kGpartN) {
+      (size_t)guess_partial_blocks(M) * kGuessFields > kGpartN) {
     set_err(err, errlen, "gcp_solve_noalloc: partial-sum area too small for M = %d", M);
     return GCP_ERR_INVALID_ARG;
   }
@@ -151,7 +153,7 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
     return GCP_OK;
   }
   launch_guess_reduce(H, h64, M, ld, gpart, s);
-  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, st, s);
+  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h64, ld, o.guess, st, s);
   launch_state_init(st, 0, s);
   launch_guess_write_d(H, h64, M, ld, D0, 1, M, M, st, s);
   NA_CK(cudaPeekAtLastError());
@@ -167,6 +169,7 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
   ctl.endgame = 0;
   ctl.tol = o.tol;
   ctl.u = kU64;
+  ctl.method = o.method;
   double* buf[2] = {D0, D1};
   const int cap = (o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
   for (int it = 0; it < cap; ++it) {
@@ -197,6 +200,7 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
     res->c_last = hs.c;
     res->mu = hs.mu;
     res->beta2 = hs.beta2;
+    res->alpha = hs.alpha;
     res->hmin = hs.hmin;
     res->hmax = hs.hmax;
   }

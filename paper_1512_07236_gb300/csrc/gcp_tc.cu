@@ -27,10 +27,13 @@
 // partial sums Tr X, Tr Sigma, sum Sigma o X, ||S - D||_F^2 (elementwise,
 // S - D = Sigma - X - theta(1-theta) J) and optionally sum D o H, from which
 // the control kernel forms Tr D, Tr D^2, Tr D^3 (Eq. mcwgamb).
-// GEMM2 (Z = X Sigma).  D_{n+1} = a D + b S - 2 D S with a = 1 - 2c,
-// b = 2 + 2c (Eq. hpcp3) becomes, for X_{n+1} = D_{n+1} - theta J,
-//   X_{n+1} = 2 theta (1-theta)(theta - c) J + (a - 2 theta^2) X
-//             + (b - 2 theta) Sigma - 2 Z.
+// GEMM2 (Z = X Sigma).  D_{n+1} = a D + b S + g3 D S (HPCP, Eq. hpcp3:
+// a = 1 - 2c, b = 2 + 2c, g3 = -2; PMCP, Eq. pm1, other coefficients)
+// becomes, for X_{n+1} = D_{n+1} - theta J, with D S = theta^3 J +
+// theta^2 X + theta Sigma + Z,
+//   X_{n+1} = xshift J + (a + g3 theta^2) X + (b + g3 theta) Sigma + g3 Z,
+//   xshift = a theta + b theta^2 + g3 theta^3 - theta
+//          (= 2 theta (1-theta)(theta - c) for HPCP).
 //
 // Schedule.  Persistent CTAs (one per SM) walk the 128 x 256 tiles of the
 // upper block triangle.  Warp 0 lane 0 issues TMA loads (SWIZZLE_64B,
@@ -120,7 +123,8 @@ __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
 template <int MODE, bool BF16>
 __device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base, bool diag_blk,
                                              const float (&acc)[128], bool mma_valid,
-                                             float ca, float cb, float cj, double (&dpart)[5]) {
+                                             float ca, float cb, float cj, float cz,
+                                             double (&dpart)[5]) {
   using HT = typename Split<BF16>::T;
   if constexpr (MODE == 3) {
     // McWeeny refinement step in FP64 (Eq. mcweeny3): with S = D^2 exact
@@ -209,7 +213,7 @@ __device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base,
         if (mma_valid) {
           const float z = acc[sub * 16 + k] * ep.inv_s2;
           const bool on_diag = diag_blk && (c0 + k == row) && in_m;
-          o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], -2.f * z)) + (on_diag ? cj : 0.f);
+          o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], cz * z)) + (on_diag ? cj : 0.f);
         } else {
           o[k] = x[k];
         }
@@ -265,7 +269,7 @@ struct TileCtx {
   bool mma;   // products needed (false: identity copy of the iterate)
   const CUtensorMap *ah, *al, *bh, *bl;
   Epi ep;
-  float ca, cb, cj;
+  float ca, cb, cj, cz;
 };
 
 template <int MODE, bool BATCHED>
@@ -316,12 +320,13 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
   const State* st = c.ep.st;
   c.mma = !c.skip && (MODE == 1 || st->apply != 0);
   c.nkb = c.mma ? c.ep.Mp / BK : 0;
-  c.ca = c.cb = c.cj = 0.f;
+  c.ca = c.cb = c.cj = c.cz = 0.f;
   if (MODE == 2 && !c.skip) {
-    const double th = st->theta;
-    c.ca = (float)(st->a - 2.0 * th * th);
-    c.cb = (float)(st->b - 2.0 * th);
+    const double th = st->theta, g3 = st->g3;
+    c.ca = (float)(st->a + g3 * th * th);
+    c.cb = (float)(st->b + g3 * th);
     c.cj = (float)st->xshift;
+    c.cz = (float)g3;
   }
 }
 
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int jb = 2 * c.J + half;
       if (ok && jb >= c.I)
         epilogue_row<MODE, BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128,
-                                 jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, dpart);
+                                 jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, c.cz, dpart);
       if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) dpart[k] = warp_sum(dpart[k]);

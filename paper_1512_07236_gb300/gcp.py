@@ -23,6 +23,8 @@ F64, F32 = 0, 1
 # gcp_precision
 PRECISIONS = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "mixed_fp16": 3, "mixed_bf16": 4}
 STOPS = {"idem_fro": 0, "trace": 1}
+GUESSES = {"canonical": 0, "hpcp+": 1, "hole": 2}
+METHODS = {"hpcp": 0, "pmcp": 1}
 HISTORY_FIELDS = 8
 EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destroy",
            "gcp_last_error", "gcp_init_guess", "gcp_step", "gcp_solve", "gcp_get_history",
@@ -33,7 +35,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("stop", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("fixed_iters", C.c_int), ("ckpt_every", C.c_int),
                 ("history_cap", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p),
-                ("refine", C.c_int)]
+                ("refine", C.c_int), ("guess", C.c_int), ("method", C.c_int)]
 
 
 class Result(C.Structure):
@@ -41,7 +43,7 @@ class Result(C.Structure):
                 ("iters_fp64", C.c_int), ("trace", C.c_double), ("energy", C.c_double),
                 ("idem_fro", C.c_double), ("trace_ddbar", C.c_double), ("c_last", C.c_double),
                 ("mu", C.c_double), ("beta2", C.c_double), ("hmin", C.c_double),
-                ("hmax", C.c_double)]
+                ("hmax", C.c_double), ("alpha", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,7 +117,7 @@ def _check_matrix(t: torch.Tensor, name: str):
 
 def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_iters=0,
                  ckpt_every=8, history_cap=0, use_graph=True, stream=None,
-                 refine="slices") -> Options:
+                 refine="slices", guess="canonical", method="hpcp") -> Options:
     lib = load_library()
     o = Options()
     lib.gcp_default_options(C.byref(o))
@@ -128,6 +130,8 @@ def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_it
     o.history_cap = int(history_cap)
     o.use_graph = 1 if use_graph else 0
     o.refine = {"slices": 0, "fp64": 1}[refine] if isinstance(refine, str) else int(refine)
+    o.guess = GUESSES[guess] if isinstance(guess, str) else int(guess)
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
