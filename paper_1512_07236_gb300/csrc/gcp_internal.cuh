@@ -135,9 +135,11 @@ void launch_convert(const void* in, int in_f64, int ldi, void* out, int out_f64,
 struct TcOperands;  // opaque: tensor maps for one (hi, lo) pair
 int tc_pad(int M);
 int tc_num_tiles(int Mp);
-// Tensor map (CUtensorMap) of an Mp x Mp 16-bit row-major operand, 128 x 32
-// boxes, 64-byte swizzle.
-int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen);
+// Tensor map (CUtensorMap) of an Mp x Mp 16-bit row-major operand, boxes of
+// 128 rows x box_k columns: box_k = 32 with 64-byte swizzle, 64 with
+// 128-byte swizzle.
+int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen,
+                  int box_k = 32);
 // Build tensor maps for a pair of split halves (Mp x Mp, row-major).
 int tc_make_operands(TcOperands** op, const void* hi, const void* lo, int Mp, int bf16,
                      char* err, int errlen);

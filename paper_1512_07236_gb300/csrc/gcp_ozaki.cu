@@ -22,9 +22,11 @@
 // 2^-53 for native FP64, at tensor-core speed.
 //
 // Kernel layout: persistent CTAs over the 128 x 256 tiles of the upper block
-// triangle; warp 0 issues TMA loads of one digit slice of the A rows and one
-// of the B rows per stage (8-stage ring of 24 KB stages), warp 1 issues one
-// MMA per 16-wide K step into one of two TMEM buffers (one buffer per pass,
+// triangle, pass-major (every CTA runs pass p over its tiles before pass
+// p + 1, so the CTAs stream the same two digit slices at a time and L2
+// holds their common panels); warp 0 issues TMA loads of one digit slice of the A rows and one
+// of the B rows per stage (4-stage ring of 48 KB stages, 64-wide K blocks in
+// 128-byte swizzled rows), warp 1 issues one MMA per 16-wide K step into one of two TMEM buffers (one buffer per pass,
 // so the MMAs of the next pass overlap the drain of this one), warps 2-9
 // drain each pass into the FP64 output.
 #include <stdio.h>
@@ -58,12 +60,16 @@ struct OzSlicePtrs {
 
 namespace {
 using namespace tcx;
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 8;
+// 64-wide K blocks in 128-byte swizzled rows: half as many TMA row
+// requests per byte as 32-wide blocks.
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int kThreads = 320;
-constexpr uint32_t kABytes = BM * BK * 2;          // 8 KB
-constexpr uint32_t kBBytes = BN * BK * 2;          // 16 KB
-constexpr uint32_t kStageBytes = kABytes + kBBytes;  // 24 KB
-constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;
+constexpr uint32_t kABytes = BM * BK * 2;          // 16 KB
+constexpr uint32_t kBBytes = BN * BK * 2;          // 32 KB
+constexpr uint32_t kStageBytes = kABytes + kBBytes;  // 48 KB
+constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per drain warp
+constexpr uint32_t kSmemBytes = STAGES * kStageBytes + kTpBytes + 1024;
+static_assert(kSmemBytes + 512 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxW = kOzSlices;  // weights 0..9
 
@@ -248,10 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t g = 0;
       bool alive = true;
-      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-        int I, J;
-        oz_tile(t, NI, NJ, I, J);
-        for (int ps = 0; ps < plan.npass && alive; ++ps)
+      for (int ps = 0; ps < plan.npass && alive; ++ps)
+        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+          int I, J;
+          oz_tile(t, NI, NJ, I, J);
           for (int p = plan.s0[ps]; p < plan.s0[ps] + plan.ns[ps] && alive; ++p)
             for (int kb = 0; kb < nkb; ++kb, ++g) {
               const int w = plan.w[ps];
@@ -279,8 +285,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_f16(0);
       uint32_t g = 0, qc = 0;
       bool alive = true;
-      for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-        for (int ps = 0; ps < plan.npass && alive; ++ps, ++qc) {
+      for (int ps = 0; ps < plan.npass && alive; ++ps) {
+        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++qc) {
           const uint32_t b = qc & 1;
           if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
             atomicOr(&st->timeout, 1);
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint32_t off = kk * 32;
-                umma(acc, sdesc(a + off), sdesc(bb + off), idesc, first ? 0u : 1u);
+                umma(acc, sdesc128(a + off), sdesc128(bb + off), idesc, first ? 0u : 1u);
                 first = false;
               }
               umma_commit(&empty_bar[s]);
@@ -318,18 +324,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     const int dw = warp - 2, q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    float* tp = reinterpret_cast<float*>(smem_raw + (sbase - raw) + STAGES * kStageBytes) +
+                dw * 32 * 32;
     uint32_t qc = 0;
     bool alive = true;
-    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-      int I, J;
-      oz_tile(t, NI, NJ, I, J);
-      const int row = I * BM + 32 * q + lane;
-      const int jb = 2 * J + half, c_base = J * BN + half * 128;
-      const bool need = jb >= I, diag = jb == I;
-      const double rs_row = row < M ? rscale[row] : 0.0;
-      for (int ps = 0; ps < plan.npass; ++ps, ++qc) {
-        const double wscale = ldexp(1.0, -5 * (plan.w[ps] + 2));  // 32^-(w+2)
-        const bool first_pass = ps == 0;
+    for (int ps = 0; ps < plan.npass && alive; ++ps) {
+      const double wscale = ldexp(1.0, -5 * (plan.w[ps] + 2));  // 32^-(w+2)
+      const bool first_pass = ps == 0, last_pass = ps == plan.npass - 1;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++qc) {
+        int I, J;
+        oz_tile(t, NI, NJ, I, J);
+        const int row = I * BM + 32 * q + lane;
+        const int jb = 2 * J + half, c_base = J * BN + half * 128;
+        const bool need = jb >= I, diag = jb == I;
+        const double rs_row = row < M ? rscale[row] : 0.0;
         const uint32_t b = qc & 1;
         const bool got = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1));
         if (!got) {
@@ -339,32 +347,55 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t base = tmem + lane_base + b * 256 + half * 128;
-#pragma unroll
+        const int row0 = I * BM + 32 * q;
+#pragma unroll 1
         for (int part = 0; part < 4; ++part) {
           uint32_t r[32];
           tmem_ld32(base + part * 32, r);
           tmem_ld_wait();
-          if (need && row < M) {
+          if (!need) continue;  // warp-uniform
+          // transpose the 32 x 32 block through shared memory (XOR-swizzled,
+          // conflict-free): lane = row -> lane = column, so that the FP64
+          // read-modify-write below is one 256-byte segment per row
+#pragma unroll
+          for (int k = 0; k < 32; ++k) tp[lane * 32 + (k ^ lane)] = __uint_as_float(r[k]);
+          __syncwarp();
+          float a[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) a[k] = tp[k * 32 + (lane ^ k)];
+          __syncwarp();
+          const int c = c_base + part * 32 + lane;
+          const double cs = c < M ? rscale[c] * wscale : 0.0;
+          double old[32];
+          if (!first_pass) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-              const int c = c_base + part * 32 + k;
-              if (c >= M || (diag && c < row)) continue;
-              const double v = (double)__uint_as_float(r[k]) * wscale * rs_row * rscale[c];
-              double* dst = S + (size_t)row * M + c;
-              *dst = first_pass ? v : *dst + v;
+              const int rk = row0 + k;
+              const bool ok = rk < M && c < M && !(diag && c < rk);
+              old[k] = ok ? S[(size_t)rk * M + c] : 0.0;
             }
+          }
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int rk = row0 + k;
+            const double rsk = __shfl_sync(0xffffffffu, rs_row, k);
+            const bool ok = rk < M && c < M && !(diag && c < rk);
+            // every factor is a power of two or an integer below 2^24: exact
+            const double v = (double)a[k] * cs * rsk;
+            if (ok) S[(size_t)rk * M + c] = first_pass ? v : old[k] + v;
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[b]);
-      }
-      // mirror the finished tile (each thread re-reads its own stores)
-      if (alive && need && row < M) {
-        for (int k = 0; k < 128; ++k) {
-          const int c = c_base + k;
-          if (c >= M || (diag && c <= row)) continue;
-          S[(size_t)c * M + row] = S[(size_t)row * M + c];
+        // mirror the finished tile (values stored by other lanes of this warp)
+        __syncwarp();
+        if (last_pass && need && row < M) {
+          for (int k = 0; k < 128; ++k) {
+            const int c = c_base + k;
+            if (c >= M || (diag && c <= row)) continue;
+            S[(size_t)c * M + row] = S[(size_t)row * M + c];
+          }
         }
       }
     }
@@ -391,7 +422,7 @@ int sm_count() {
 int oz_make_operands(OzOperands** op, void* const* slices, int Mp, char* err, int errlen) {
   OzOperands* o = new OzOperands;
   for (int s = 0; s < kOzSlices; ++s)
-    if (tc_encode_map(&o->maps.m[s], slices[s], Mp, 0, err, errlen)) {
+    if (tc_encode_map(&o->maps.m[s], slices[s], Mp, 0, err, errlen, BK)) {
       delete o;
       return 1;
     }

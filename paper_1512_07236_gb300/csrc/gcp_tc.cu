@@ -555,7 +555,9 @@ EncodeTiledFn get_encode(char* err, int errlen) {
   return fn;
 }
 
-int encode_map(CUtensorMap* m, const void* ptr, int Mp, int bf16, char* err, int errlen) {
+// box_k = 32 (64-byte rows, SWIZZLE_64B) or 64 (128-byte rows, SWIZZLE_128B).
+int encode_map(CUtensorMap* m, const void* ptr, int Mp, int bf16, char* err, int errlen,
+               int box_k = BK) {
   EncodeTiledFn enc = get_encode(err, errlen);
   if (!enc) return 1;
   if (((uintptr_t)ptr & 15u) != 0 || ((size_t)Mp * 2) % 16 != 0 || Mp % BN != 0) {
@@ -564,12 +566,16 @@ int encode_map(CUtensorMap* m, const void* ptr, int Mp, int bf16, char* err, int
   }
   cuuint64_t dims[2] = {(cuuint64_t)Mp, (cuuint64_t)Mp};
   cuuint64_t strides[1] = {(cuuint64_t)Mp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  if (box_k != 32 && box_k != 64) {
+    snprintf(err, errlen, "tensor map: unsupported box width");
+    return 1;
+  }
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)BM};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                    const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return 1;
@@ -613,8 +619,8 @@ int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const Bat
 
 int tc_pad(int M) { return ((M + BN - 1) / BN) * BN; }
 
-int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen) {
-  return encode_map((CUtensorMap*)map, ptr, Mp, bf16, err, errlen);
+int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen, int box_k) {
+  return encode_map((CUtensorMap*)map, ptr, Mp, bf16, err, errlen, box_k);
 }
 
 int tc_num_tiles(int Mp) {

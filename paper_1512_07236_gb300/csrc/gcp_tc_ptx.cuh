@@ -70,6 +70,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)4 << 61;             // SWIZZLE_64B
   return d;
 }
+// The same for K-major operands in 128-byte swizzled rows (8-row core
+// groups of 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // LBO (ignored for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // SBO
+  d |= (uint64_t)1 << 46;             // version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A/B format
 // (bits 7-9, 10-12: 0 fp16, 1 bf16), both K-major, N>>3 at bit 17,
 // M>>4 at bit 24.
