@@ -75,7 +75,14 @@ constexpr int kThreads = 320;
 constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
-constexpr uint32_t kSmemBytes = STAGES * kStageBytes + 1024;
+constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per drain warp
+// Only GEMM1's epilogue uses the transposition buffers; the other modes keep
+// that shared memory as L1 cache for their row-wise epilogue loads.
+template <int MODE>
+__host__ __device__ constexpr uint32_t smem_bytes() {
+  return STAGES * kStageBytes + (MODE == 1 ? kTpBytes : 0u) + 1024;
+}
+static_assert(smem_bytes<1>() + 768 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
 
 struct Epi {
@@ -258,6 +265,157 @@ __device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base,
         reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
       }
     }
+  }
+}
+
+// GEMM1 epilogue of one warp for one 32 x 32 block: rows row0..row0+31,
+// columns c0..c0+31, v[k] = s^2 (X X)_{row0+lane, c0+k} (lane = row, as the
+// accumulator comes out of TMEM).  The block goes through the warp's shared
+// buffer `tp` (4-float groups XOR-swizzled by row: conflict-free for float4
+// and scalar access) and is read back with eight lanes per row and four
+// consecutive columns per lane, so that the X loads and the direct stores
+// of Sigma and its halves are whole 128-byte row segments; Sigma goes back
+// to `tp` and the mirrored stores read it with eight lanes per column.
+// Blocks on the diagonal take an element-wise path (upper triangle only).
+// (GEMM2's epilogue keeps lane = row: there the transposes cost more than
+// the coalescing saves.)
+__device__ __forceinline__ int tp_idx(int r, int c) {
+  return r * 32 + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3));
+}
+
+template <bool BF16>
+__device__ __forceinline__ void store_out4(const Epi& ep, size_t off, float4 o) {
+  using HT = typename Split<BF16>::T;
+  HT h[4], l[4];
+  Split<BF16>::split(o.x * ep.split_scale, h[0], l[0]);
+  Split<BF16>::split(o.y * ep.split_scale, h[1], l[1]);
+  Split<BF16>::split(o.z * ep.split_scale, h[2], l[2]);
+  Split<BF16>::split(o.w * ep.split_scale, h[3], l[3]);
+  *reinterpret_cast<float4*>(ep.out + off) = o;
+  *reinterpret_cast<uint2*>(reinterpret_cast<HT*>(ep.out_h) + off) = *reinterpret_cast<uint2*>(h);
+  *reinterpret_cast<uint2*>(reinterpret_cast<HT*>(ep.out_l) + off) = *reinterpret_cast<uint2*>(l);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void store_out1(const Epi& ep, size_t off, float o) {
+  using HT = typename Split<BF16>::T;
+  HT h, l;
+  Split<BF16>::split(o * ep.split_scale, h, l);
+  ep.out[off] = o;
+  reinterpret_cast<HT*>(ep.out_h)[off] = h;
+  reinterpret_cast<HT*>(ep.out_l)[off] = l;
+}
+
+template <bool BF16>
+__device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, bool diag_blk,
+                                            const float* v, float (&pp)[3], double (&dpart)[5],
+                                            float* tp) {
+  const int lane = threadIdx.x & 31;
+  const int Mp = ep.Mp;
+  const double th = ep.st->theta;
+  const float f2th = (float)(2.0 * th);
+  const float thtb = (float)(th * (1.0 - th));
+  const float is2 = ep.inv_s2;
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(&tp[tp_idx(lane, 4 * g)]) =
+        make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+  __syncwarp();
+  if (!diag_blk) {
+    // every element lies above the diagonal (weight 2, mirrored)
+    const int rs = lane >> 3, cl = 4 * (lane & 7);
+    const size_t cbase = (size_t)c0 + cl;
+#pragma unroll
+    for (int jh = 0; jh < 8; jh += 4) {
+      float4 x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        x[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(row0 + rs + 4 * (jh + j)) * Mp +
+                                                cbase);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int rr = rs + 4 * (jh + j);
+        const size_t off = (size_t)(row0 + rr) * Mp + cbase;
+        const float4 a = *reinterpret_cast<const float4*>(&tp[tp_idx(rr, cl)]);
+        float4 o;
+        o.x = fmaf(f2th, x[j].x, a.x * is2);  // Sigma = 2 theta X + Y
+        o.y = fmaf(f2th, x[j].y, a.y * is2);
+        o.z = fmaf(f2th, x[j].z, a.z * is2);
+        o.w = fmaf(f2th, x[j].w, a.w * is2);
+        const float ex = o.x - x[j].x, ey = o.y - x[j].y, ez = o.z - x[j].z, ew = o.w - x[j].w;
+        pp[0] += 2.f * (o.x * x[j].x + o.y * x[j].y + o.z * x[j].z + o.w * x[j].w);
+        pp[1] += 2.f * (ex * ex + ey * ey + ez * ez + ew * ew);
+        if (ep.H) {
+          const int r = row0 + rr;
+          const float xs[4] = {x[j].x, x[j].y, x[j].z, x[j].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int cc = c0 + cl + i;
+            if (r < ep.M && cc < ep.M) {
+              const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + cc]
+                                        : (double)((const float*)ep.H)[(size_t)r * ep.ldh + cc];
+              pp[2] += 2.f * xs[i] * (float)h;
+            }
+          }
+        }
+        store_out4<BF16>(ep, off, o);
+        *reinterpret_cast<float4*>(&tp[tp_idx(rr, cl)]) = o;
+      }
+    }
+    __syncwarp();
+    // mirror: eight lanes per original column, four consecutive rows each
+    const int cs = lane >> 3, gr = lane & 7;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = cs + 4 * j;
+      const float4 m = make_float4(tp[tp_idx(4 * gr, cc)], tp[tp_idx(4 * gr + 1, cc)],
+                                   tp[tp_idx(4 * gr + 2, cc)], tp[tp_idx(4 * gr + 3, cc)]);
+      store_out4<BF16>(ep, (size_t)(c0 + cc) * Mp + row0 + 4 * gr, m);
+    }
+    __syncwarp();
+  } else {
+    // diagonal block: lane = column, element (row0 + k, c0 + lane)
+    const int c = c0 + lane;
+    float o[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int r = row0 + k;
+      const bool keep = c >= r;
+      const bool on_diag = c == r && r < ep.M;
+      const size_t off = (size_t)r * Mp + c;
+      const float a = tp[tp_idx(k, lane)];
+      const float x = ep.X[off];
+      const float sg = fmaf(f2th, x, a * is2);
+      // weight: an element above the diagonal stands for its mirror too
+      const float w = keep ? (c == r ? 1.f : 2.f) : 0.f;
+      const float e = sg - x - (on_diag ? thtb : 0.f);  // (S - D)_rc
+      pp[0] += w * sg * x;
+      pp[1] += w * e * e;
+      if (on_diag) {
+        dpart[0] += (double)x;
+        dpart[1] += (double)sg;
+      }
+      if (ep.H && r < ep.M && c < ep.M) {
+        const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + c]
+                                  : (double)((const float*)ep.H)[(size_t)r * ep.ldh + c];
+        const float d = x + (on_diag ? (float)th : 0.f);
+        pp[2] += w * d * (float)h;
+      }
+      o[k] = sg;
+      if (keep) store_out1<BF16>(ep, off, sg);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) tp[tp_idx(k, lane)] = o[k];
+    __syncwarp();
+    const int r = row0 + lane;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int cc = c0 + k;
+      if (cc <= r) continue;
+      store_out1<BF16>(ep, (size_t)cc * Mp + r, tp[tp_idx(lane, k)]);
+    }
+    __syncwarp();
   }
 }
 
@@ -461,6 +619,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // TMEM lane quarter is fixed by the warp's rank within its warpgroup
     const int dw = warp - 2, q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    float* tp = reinterpret_cast<float*>(smem_raw + (sbase - raw) + STAGES * kStageBytes) +
+                dw * 32 * 32;
     uint32_t qc = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
@@ -501,9 +661,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool ok = alive && !(*(volatile int*)timeout_flag);
       double dpart[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       const int jb = 2 * c.J + half;
-      if (ok && jb >= c.I)
-        epilogue_row<MODE, BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128,
-                                 jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, c.cz, dpart);
+      if (ok && jb >= c.I) {
+        if constexpr (MODE == 1) {
+          float pp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int part = 0; part < 4; ++part)
+            gemm1_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
+                              jb == c.I, &acc[part * 32], pp, dpart, tp);
+          dpart[2] += (double)pp[0];
+          dpart[3] += (double)pp[1];
+          dpart[4] += (double)pp[2];
+        } else {
+          epilogue_row<MODE, BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128,
+                                   jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, c.cz, dpart);
+        }
+      }
       if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) dpart[k] = warp_sum(dpart[k]);
@@ -599,7 +771,8 @@ int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const Bat
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, BF16, BATCHED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_bytes<MODE>());
     if (e != cudaSuccess) return 1;
     attr = true;
   }
@@ -607,10 +780,10 @@ int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const Bat
   if (BATCHED) {
     CUtensorMap dummy;
     memset(&dummy, 0, sizeof dummy);
-    tc_gemm_kernel<MODE, BF16, true><<<grid, kThreads, kSmemBytes, s>>>(dummy, dummy, dummy, dummy,
-                                                                        ep, items, tile_inst);
+    tc_gemm_kernel<MODE, BF16, true><<<grid, kThreads, smem_bytes<MODE>(), s>>>(
+        dummy, dummy, dummy, dummy, ep, items, tile_inst);
   } else {
-    tc_gemm_kernel<MODE, BF16, false><<<grid, kThreads, kSmemBytes, s>>>(A->hi, A->lo, B->hi, B->lo,
+    tc_gemm_kernel<MODE, BF16, false><<<grid, kThreads, smem_bytes<MODE>(), s>>>(A->hi, A->lo, B->hi, B->lo,
                                                                          ep, nullptr, nullptr);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
