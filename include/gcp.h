@@ -97,9 +97,8 @@ typedef struct {
   int refine;          /* mixed modes, refinement products: 0 (default) exact
                           digit-slice products on the tensor cores with
                           McWeeny steps (M <= 29000, no fixed_iters;
-                          gcp_solve only);  1 FP64 SIMT products and HPCP
-                          steps (always used otherwise, and by
-                          gcp_solve_batched) */
+                          gcp_solve and gcp_solve_batched);  1 FP64 SIMT
+                          products and HPCP steps (always used otherwise) */
   int guess;           /* gcp_guess (default GCP_GUESS_CANONICAL) */
   int method;          /* gcp_method (default GCP_METHOD_HPCP) */
 } gcp_options;

@@ -801,7 +801,10 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   std::vector<BatchItem> items(nb);
   std::vector<size_t> inst_off(nb);
   size_t off = al(sizeof(State) * (size_t)nb);  // states first, contiguous
-  int ntc = 0, nf64 = 0, maxM = 0;
+  int ntc = 0, nf64 = 0, noz = 0, maxM = 0;
+  for (int k = 0; k < nb; ++k) maxM = M[idx[k]] > maxM ? M[idx[k]] : maxM;
+  // the refinement of the mixed modes: exact digit slices as in gcp_solve
+  const bool oz = mixed && o.refine == 0 && o.fixed_iters == 0 && maxM <= 29000;
   for (int k = 0; k < nb; ++k) {
     const int b = idx[k];
     BatchItem& it = items[k];
@@ -830,7 +833,15 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       it.f64_n = batch_f64_tiles(it.M);
       nf64 += it.f64_n;
     }
+    if (oz) {
+      const size_t n2 = (size_t)it.Mp * it.Mp;
+      off += al(oz_batch_map_bytes()) + (kOzSlices + 4) * al(n2 * 2) +
+             2 * al((size_t)it.Mp * 8);
+      it.oz_off = noz;
+      noz += it.M < 1024 ? it.M : 1024;
+    }
   }
+  const int nslots = ntc > nf64 ? (ntc > noz ? ntc : noz) : (nf64 > noz ? nf64 : noz);
   const size_t items_off = off;
   off += al(sizeof(BatchItem) * (size_t)nb);
   const size_t tinst_tc_off = off;
@@ -838,7 +849,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   const size_t tinst_f64_off = off;
   off += al(sizeof(int) * (size_t)(nf64 > 0 ? nf64 : 1));
   const size_t part_off = off;
-  off += al(sizeof(double) * kPartFields * (size_t)(ntc > nf64 ? ntc : nf64));
+  off += al(sizeof(double) * kPartFields * (size_t)nslots);
   const size_t gpart_off = off;
   const int gstride = guess_partial_blocks(maxM);
   off += al(sizeof(double) * kGuessFields * (size_t)gstride * (size_t)nb);
@@ -932,6 +943,29 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
         p += al(m2 * 8);
         for (int t = 0; t < it.f64_n; ++t) tf[it.f64_off + t] = k;
       }
+      if (oz) {
+        const size_t n2 = (size_t)it.Mp * it.Mp;
+        char* omaps_dev = p;
+        p += al(oz_batch_map_bytes());
+        for (int sl = 0; sl < kOzSlices; ++sl) {
+          it.oz_sl[sl] = p;
+          p += al(n2 * 2);
+        }
+        void** halves[4] = {&it.oz_dh, &it.oz_dl, &it.oz_xh, &it.oz_xl};
+        for (int hk = 0; hk < 4; ++hk) {
+          *halves[hk] = p;
+          p += al(n2 * 2);
+        }
+        it.oz_rs = (double*)p;
+        p += al((size_t)it.Mp * 8);
+        it.oz_xs = (double*)p;
+        p += al((size_t)it.Mp * 8);
+        std::vector<char> om(oz_batch_map_bytes());
+        if (oz_build_batch_maps(om.data(), it, errbuf, sizeof errbuf))
+          return fail(h, GCP_ERR_CUDA, "gcp_solve_batched: %s", errbuf);
+        CK(cudaMemcpy(omaps_dev, om.data(), om.size(), cudaMemcpyHostToDevice));
+        it.oz_maps = omaps_dev;
+      }
     }
     CK(cudaMemcpy(items_d, items.data(), sizeof(BatchItem) * nb, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(tinst_tc, tt.data(), sizeof(int) * tt.size(), cudaMemcpyHostToDevice));
@@ -951,6 +985,8 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   c0.final_phase = 1;
   c0.endgame = split ? 1 : 0;
   c0.u = kU64;
+  c0.mcw_only = oz ? 1 : 0;
+  c1.method = c0.method = o.method;
 
   auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
     if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, ss))
@@ -966,6 +1002,19 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
     launch_batch_f64_gemm1(items_d, nb, tinst_f64, nf64, part, ss);
     launch_batch_control(part, items_d, nb, c0, ss);
     launch_batch_f64_gemm2(items_d, nb, tinst_f64, nf64, ss);
+    launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
+    CK(cudaPeekAtLastError());
+    return GCP_OK;
+  };
+  // exact-slice refinement step, as rec_oz_step of a single solve
+  auto oz_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
+    launch_batch_oz_slice(items_d, nb, tc_pad(maxM), ss);
+    if (launch_batch_oz_gemm(items_d, tinst_tc, ntc, maxM, ss))
+      return fail(h, GCP_ERR_CUDA, "batched slice GEMM launch failed");
+    launch_batch_oz_finalize(items_d, nb, maxM, part, ss);
+    launch_batch_control(part, items_d, nb, c0, ss);
+    if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, ss))
+      return fail(h, GCP_ERR_CUDA, "batched refinement product launch failed");
     launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
     CK(cudaPeekAtLastError());
     return GCP_OK;
@@ -1022,7 +1071,11 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       launch_batch_x_to_d64(items_d, nb, maxM, ss);
       launch_batch_phase_begin(items_d, nb, 0, ss);
     }
-    if ((!split || mixed) && (rr = run_phase(f64_body, ss, graph)) != GCP_OK) return rr;
+    if (oz) {
+      if ((rr = run_phase(oz_body, ss, graph)) != GCP_OK) return rr;
+    } else if ((!split || mixed) && (rr = run_phase(f64_body, ss, graph)) != GCP_OK) {
+      return rr;
+    }
     launch_batch_copy_out(items_d, nb, maxM, split && !mixed ? 1 : 0, d64, ss);
     launch_batch_energy(items_d, nb, d64, h64, gpart, gstride, ss);
     CK(cudaPeekAtLastError());

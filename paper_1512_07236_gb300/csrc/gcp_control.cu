@@ -281,8 +281,10 @@ __global__ void __launch_bounds__(kCtlThreads) batch_control_kernel(const double
                                                                     Ctl ctl) {
   __shared__ double red[32 * 5];
   const BatchItem& it = items[blockIdx.x];
-  const int off = ctl.phase == 1 ? it.tc_off : it.f64_off;
-  const int n = ctl.phase == 1 ? it.tc_n : it.f64_n;
+  // partial-sum slots: the tensor-core tiles (split phase), the FP64 tiles,
+  // or the exact-slice finalize blocks (refinement with mcw_only)
+  const int off = ctl.phase == 1 ? it.tc_off : (ctl.mcw_only ? it.oz_off : it.f64_off);
+  const int n = ctl.phase == 1 ? it.tc_n : (ctl.mcw_only ? (it.M < 1024 ? it.M : 1024) : it.f64_n);
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const double* p = part + (size_t)(off + t) * kPartFields;

@@ -54,6 +54,11 @@ struct Ctl {
 // Number of partial-sum fields written per GEMM1 tile.
 constexpr int kPartFields = 6;  // T1, T2, T3, R^2, E, spare
 
+// Digit slices of the exact-slice refinement and the scale of its fp16
+// operand halves (gcp_ozaki.cu).
+constexpr int kOzSlices = 9;
+constexpr double kRefScale = 16384.0;  // 2^14
+
 // Per-instance descriptor of a batched solve (device memory).  Every
 // instance has its own state, buffers and slices of the batched work lists.
 // The iterate buffer in use is State::parity: GEMM1 reads buffer `parity`;
@@ -77,6 +82,15 @@ struct BatchItem {
   int f64_off, f64_n;  // FP64 tiles in the batched work list
   int gblocks;         // reduction blocks of the guess/energy passes
                        // (guess_partial_blocks(M): the single-solve layout)
+  // exact-slice refinement (mixed modes): digit slices, row scales of D and
+  // of X = S - D, fp16 halves of both, and 13 tensor maps (the 9 slices with
+  // 64-wide boxes, then D hi, D lo, X hi, X lo with 32-wide boxes)
+  void* oz_sl[kOzSlices];
+  double* oz_rs;
+  double* oz_xs;
+  void *oz_dh, *oz_dl, *oz_xh, *oz_xl;
+  const void* oz_maps;
+  int oz_off;  // first partial-sum slot (min(M, 1024) slots, as a single solve)
 };
 
 // ---- guess (gcp_guess.cu) ------------------------------------------------
@@ -165,8 +179,6 @@ int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const doub
 // D (FP64, M x M) -> per-row scale 2^e_i with |D_ij| <= 2^e_i / 2, nine
 // signed base-32 digit slices (fp16, Mp x Mp) and the fp16 halves of
 // kRefScale D_ij / 2^e_i (the D operand of the refinement product).
-constexpr int kOzSlices = 9;
-constexpr double kRefScale = 16384.0;  // 2^14
 struct OzOperands;  // opaque: tensor maps of the nine slices
 int oz_make_operands(OzOperands** op, void* const* slices, int Mp, char* err, int errlen);
 void oz_free_operands(OzOperands* op);
@@ -181,6 +193,15 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
 int oz_finalize_blocks(int M);
 void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s);
+// Batched forms over the instances' BatchItem (work list: the tensor-core
+// tiles), reading and writing the current iterate D64[State::parity].
+void launch_batch_oz_slice(const BatchItem* items, int batch, int maxMp, cudaStream_t s);
+int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntiles, int maxM,
+                         cudaStream_t s);
+void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
+                              cudaStream_t s);
+size_t oz_batch_map_bytes();
+int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int errlen);
 
 // ---- adjoint (gcp_adjoint.cu) --------------------------------------------
 constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24

@@ -93,16 +93,12 @@ __device__ __forceinline__ void oz_tile(int t, int NI, int NJ, int& I, int& J) {
 // gives the 45-bit fixed-point value n = rint(2^45 D_ij / 2^e_i), |n| <= 2^44,
 // and its balanced base-32 digits follow by rounding shifts, most
 // significant first, each remainder exact.
-__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ D, int M, int Mp,
-                                                       const OzSlicePtrs slices,
-                                                       double* __restrict__ rscale,
-                                                       __half* __restrict__ Dh,
-                                                       __half* __restrict__ Dl,
-                                                       const State* __restrict__ st) {
-  if (st->stopped) return;
+// One row i of D (the whole block works on it).
+__device__ __forceinline__ void slice_row(const double* __restrict__ D, int M, int Mp, int i,
+                                          __half* const* sl, double* __restrict__ rscale,
+                                          __half* __restrict__ Dh, __half* __restrict__ Dl) {
   __shared__ unsigned long long red[32];
   __shared__ int e_sh;
-  const int i = blockIdx.x;
   // row max of |D_ij| as the largest magnitude bit pattern (monotone for
   // non-negative doubles)
   unsigned long long mb = 0ull;
@@ -148,24 +144,43 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
       const int k = 5 * (kOzSlices - 1 - s);
       const long long dg = k > 0 ? ((n + (1ll << (k > 0 ? k - 1 : 0))) >> k) : n;  // |dg| <= 16
       n -= dg << k;  // exact, |n| <= 2^(k-1)
-      slices.p[s][o] = __int2half_rn((int)dg);
+      sl[s][o] = __int2half_rn((int)dg);
     }
   }
+}
+
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ D, int M, int Mp,
+                                                       const OzSlicePtrs slices,
+                                                       double* __restrict__ rscale,
+                                                       __half* __restrict__ Dh,
+                                                       __half* __restrict__ Dl,
+                                                       const State* __restrict__ st) {
+  if (st->stopped) return;
+  slice_row(D, M, Mp, blockIdx.x, slices.p, rscale, Dh, Dl);
+}
+
+// Batched: block (i, instance); D is the instance's current iterate.
+__global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* items) {
+  const BatchItem& it = items[blockIdx.y];
+  if ((int)blockIdx.x >= it.Mp || it.st->stopped) return;
+  slice_row(it.D64[it.st->parity], it.M, it.Mp, blockIdx.x, (__half* const*)it.oz_sl, it.oz_rs,
+            (__half*)it.oz_dh, (__half*)it.oz_dl);
 }
 
 // ---- finalize: traces, residual, halves of X = S - D -----------------------
 // Row i of X is scaled by xscale_i = 2^(13 - e) with max_j |X_ij| < 2^e, so
 // that its fp16 halves keep ~22 bits of every row whatever the size of X.
 constexpr int kFinThreads = 256;
-__global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
-    const double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
-    double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
-    double* __restrict__ xscale, const State* __restrict__ st) {
-  if (st->stopped) return;
+// Block `blk` of `nblk`: rows blk, blk + nblk, ...; partials into part[0..5].
+__device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
+                                              const double* __restrict__ D, int M, int Mp,
+                                              int blk, int nblk, double* __restrict__ part,
+                                              __half* __restrict__ Xh, __half* __restrict__ Xl,
+                                              double* __restrict__ xscale) {
   __shared__ double red[32 * 5];
   __shared__ double mred[32];
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int i = blockIdx.x; i < Mp; i += gridDim.x) {
+  for (int i = blk; i < Mp; i += nblk) {
     double mx = 0.0;
     if (i < M)
       for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -203,19 +218,78 @@ __global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
   }
   block_sum<5>(v, red);
   if (threadIdx.x == 0) {
-    double* p = part + (size_t)blockIdx.x * kPartFields;
-    for (int k = 0; k < 5; ++k) p[k] = v[k];
-    p[5] = 0.0;
+    for (int k = 0; k < 5; ++k) part[k] = v[k];
+    part[5] = 0.0;
   }
 }
 
+__global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
+    const double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
+    double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
+    double* __restrict__ xscale, const State* __restrict__ st) {
+  if (st->stopped) return;
+  finalize_rows(S, D, M, Mp, blockIdx.x, gridDim.x, part + (size_t)blockIdx.x * kPartFields, Xh,
+                Xl, xscale);
+}
+
+// Batched: block (b, instance), the same row partition as a single solve of
+// that instance (oz_finalize_blocks(M) blocks), partials at the instance's
+// slots from oz_off.
+__global__ void __launch_bounds__(kFinThreads) batch_oz_finalize_kernel(const BatchItem* items,
+                                                                        double* __restrict__ part) {
+  const BatchItem& it = items[blockIdx.y];
+  const int nblk = it.M < 1024 ? it.M : 1024;
+  if ((int)blockIdx.x >= nblk || it.st->stopped) return;
+  finalize_rows(it.S64, it.D64[it.st->parity], it.M, it.Mp, blockIdx.x, nblk,
+                part + (size_t)(it.oz_off + blockIdx.x) * kPartFields, (__half*)it.oz_xh,
+                (__half*)it.oz_xl, it.oz_xs);
+}
+
 // ---- the exact slice GEMM ---------------------------------------------------
+// One tile of the work: its block coordinates and its instance's operands.
+struct OzTile {
+  int I, J, M, Mp;
+  const CUtensorMap* maps;
+  const double* rscale;
+  double* S;
+  bool skip;  // batched: the instance has stopped
+};
+
+template <bool BATCHED>
+__device__ __forceinline__ void oz_ctx(int t, const CUtensorMap* maps, const double* rscale,
+                                       double* S, int M, int Mp, const BatchItem* items,
+                                       const int* tile_inst, OzTile& c) {
+  if (!BATCHED) {
+    c.M = M;
+    c.Mp = Mp;
+    c.maps = maps;
+    c.rscale = rscale;
+    c.S = S;
+    c.skip = false;
+    oz_tile(t, Mp / BM, Mp / BN, c.I, c.J);
+  } else {
+    const BatchItem& it = items[tile_inst[t]];
+    c.skip = it.st->stopped != 0;
+    c.M = it.M;
+    c.Mp = it.Mp;
+    c.maps = (const CUtensorMap*)it.oz_maps;
+    c.rscale = it.oz_rs;
+    c.S = it.S64;
+    oz_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
+  }
+}
+
+// Single solve: `maps`, `rscale`, `S`, M, Mp and `st` describe the one
+// instance.  Batched: the work list `tile_inst` (the tensor-core tile list of
+// the batch) names each tile's instance; every instance's operands come from
+// its BatchItem, and tiles of stopped instances are skipped.
+template <bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ OzPlan plan,
                    const double* __restrict__ rscale, double* __restrict__ S, int M, int Mp,
-                   int ntiles, State* st) {
-  if (st->stopped || st->timeout) return;
-  const int NI = Mp / BM, NJ = Mp / BN;
+                   int ntiles, State* st, const BatchItem* items, const int* tile_inst) {
+  if (!BATCHED && (st->stopped || st->timeout)) return;
+  int* const tflag = BATCHED ? &items[0].st->timeout : &st->timeout;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -248,7 +322,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  const int nkb = Mp / BK;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -256,29 +329,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool alive = true;
       for (int ps = 0; ps < plan.npass && alive; ++ps)
         for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-          int I, J;
-          oz_tile(t, NI, NJ, I, J);
+          OzTile c;
+          oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
+          if (c.skip) continue;
+          const int nkb = c.Mp / BK;
           for (int p = plan.s0[ps]; p < plan.s0[ps] + plan.ns[ps] && alive; ++p)
             for (int kb = 0; kb < nkb; ++kb, ++g) {
               const int w = plan.w[ps];
               const uint32_t s = g % STAGES;
               if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1)) {
-                atomicOr(&st->timeout, 1);
+                atomicOr(tflag, 1);
                 alive = false;
                 break;
               }
               const uint32_t stage = sbase + s * kStageBytes;
               mbar_expect_tx(&full_bar[s], kStageBytes);
               const int kx = kb * BK;
-              tma_load_2d(&maps.m[p], &full_bar[s], stage, kx, I * BM);
-              tma_load_2d(&maps.m[w - p], &full_bar[s], stage + kABytes, kx, J * BN);
-              tma_load_2d(&maps.m[w - p], &full_bar[s], stage + kABytes + kBBytes / 2, kx,
-                          J * BN + 128);
+              tma_load_2d(&c.maps[p], &full_bar[s], stage, kx, c.I * BM);
+              tma_load_2d(&c.maps[w - p], &full_bar[s], stage + kABytes, kx, c.J * BN);
+              tma_load_2d(&c.maps[w - p], &full_bar[s], stage + kABytes + kBBytes / 2, kx,
+                          c.J * BN + 128);
             }
-      }
+        }
       const uint32_t first = g > STAGES ? g - STAGES : 0;
       for (uint32_t k = first; k < g; ++k)
-        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(&st->timeout, 1);
+        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(tflag, 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -286,10 +361,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t g = 0, qc = 0;
       bool alive = true;
       for (int ps = 0; ps < plan.npass && alive; ++ps) {
-        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++qc) {
+        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+          OzTile c;
+          oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
+          if (c.skip) continue;
+          const int nkb = c.Mp / BK;
           const uint32_t b = qc & 1;
           if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
-            atomicOr(&st->timeout, 1);
+            atomicOr(tflag, 1);
             alive = false;
             break;
           }
@@ -300,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = 0; kb < nkb; ++kb, ++g) {
               const uint32_t s = g % STAGES;
               if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
-                atomicOr(&st->timeout, 1);
+                atomicOr(tflag, 1);
                 alive = false;
                 break;
               }
@@ -316,10 +395,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               umma_commit(&empty_bar[s]);
             }
           umma_commit(&accf_bar[b]);
+          ++qc;
         }
       }
       umma_commit(&fin_bar);
-      if (!mbar_wait(&fin_bar, 0)) atomicOr(&st->timeout, 1);
+      if (!mbar_wait(&fin_bar, 0)) atomicOr(tflag, 1);
     }
   } else {
     const int dw = warp - 2, q = warp & 3, half = dw >> 2;
@@ -331,23 +411,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int ps = 0; ps < plan.npass && alive; ++ps) {
       const double wscale = ldexp(1.0, -5 * (plan.w[ps] + 2));  // 32^-(w+2)
       const bool first_pass = ps == 0, last_pass = ps == plan.npass - 1;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++qc) {
-        int I, J;
-        oz_tile(t, NI, NJ, I, J);
-        const int row = I * BM + 32 * q + lane;
-        const int jb = 2 * J + half, c_base = J * BN + half * 128;
-        const bool need = jb >= I, diag = jb == I;
-        const double rs_row = row < M ? rscale[row] : 0.0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        OzTile c;
+        oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
+        if (c.skip) continue;
+        const int Mi = c.M;
+        double* const Si = c.S;
+        const int row = c.I * BM + 32 * q + lane;
+        const int jb = 2 * c.J + half, c_base = c.J * BN + half * 128;
+        const bool need = jb >= c.I, diag = jb == c.I;
+        const double rs_row = row < Mi ? c.rscale[row] : 0.0;
         const uint32_t b = qc & 1;
         const bool got = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1));
         if (!got) {
-          if (lane == 0) atomicOr(&st->timeout, 1);
+          if (lane == 0) atomicOr(tflag, 1);
           alive = false;
           break;
         }
         tc_fence_after();
         const uint32_t base = tmem + lane_base + b * 256 + half * 128;
-        const int row0 = I * BM + 32 * q;
+        const int row0 = c.I * BM + 32 * q;
 #pragma unroll 1
         for (int part = 0; part < 4; ++part) {
           uint32_t r[32];
@@ -364,37 +447,38 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < 32; ++k) a[k] = tp[k * 32 + (lane ^ k)];
           __syncwarp();
-          const int c = c_base + part * 32 + lane;
-          const double cs = c < M ? rscale[c] * wscale : 0.0;
+          const int cc = c_base + part * 32 + lane;
+          const double cs = cc < Mi ? c.rscale[cc] * wscale : 0.0;
           double old[32];
           if (!first_pass) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
               const int rk = row0 + k;
-              const bool ok = rk < M && c < M && !(diag && c < rk);
-              old[k] = ok ? S[(size_t)rk * M + c] : 0.0;
+              const bool ok = rk < Mi && cc < Mi && !(diag && cc < rk);
+              old[k] = ok ? Si[(size_t)rk * Mi + cc] : 0.0;
             }
           }
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const int rk = row0 + k;
             const double rsk = __shfl_sync(0xffffffffu, rs_row, k);
-            const bool ok = rk < M && c < M && !(diag && c < rk);
+            const bool ok = rk < Mi && cc < Mi && !(diag && cc < rk);
             // every factor is a power of two or an integer below 2^24: exact
             const double v = (double)a[k] * cs * rsk;
-            if (ok) S[(size_t)rk * M + c] = first_pass ? v : old[k] + v;
+            if (ok) Si[(size_t)rk * Mi + cc] = first_pass ? v : old[k] + v;
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[b]);
+        ++qc;
         // mirror the finished tile (values stored by other lanes of this warp)
         __syncwarp();
-        if (last_pass && need && row < M) {
+        if (last_pass && need && row < Mi) {
           for (int k = 0; k < 128; ++k) {
-            const int c = c_base + k;
-            if (c >= M || (diag && c <= row)) continue;
-            S[(size_t)c * M + row] = S[(size_t)row * M + c];
+            const int col = c_base + k;
+            if (col >= Mi || (diag && col <= row)) continue;
+            Si[(size_t)col * Mi + row] = Si[(size_t)row * Mi + col];
           }
         }
       }
@@ -471,7 +555,7 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
                    State* st, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmemBytes) != cudaSuccess)
       return 1;
     attr = true;
@@ -480,9 +564,53 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
   const int grid = ntiles < sm_count() ? ntiles : sm_count();
   OzPlan plan;
   if (oz_plan(M, &plan)) return 1;
-  oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(op->maps, plan, rscale, S64, M, Mp, ntiles,
-                                                    st);
+  oz_gemm_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(op->maps, plan, rscale, S64, M, Mp,
+                                                           ntiles, st, nullptr, nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntiles, int maxM,
+                         cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess)
+      return 1;
+    attr = true;
+  }
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  // the pass plan of the largest instance is valid for every smaller one
+  // (and equal to theirs up to M = 7281, where every weight fits one pass)
+  OzPlan plan;
+  if (oz_plan(maxM, &plan)) return 1;
+  OzMaps none;
+  memset(&none, 0, sizeof none);
+  oz_gemm_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(none, plan, nullptr, nullptr, 0, 0,
+                                                          ntiles, nullptr, items, tile_inst);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
+}
+
+void launch_batch_oz_slice(const BatchItem* items, int batch, int maxMp, cudaStream_t s) {
+  dim3 g(maxMp, batch);
+  batch_oz_slice_kernel<<<g, 256, 0, s>>>(items);
+}
+
+void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
+                              cudaStream_t s) {
+  dim3 g(maxM < 1024 ? maxM : 1024, batch);
+  batch_oz_finalize_kernel<<<g, kFinThreads, 0, s>>>(items, part);
+}
+
+size_t oz_batch_map_bytes() { return (kOzSlices + 4) * sizeof(CUtensorMap); }
+
+int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int errlen) {
+  CUtensorMap* m = (CUtensorMap*)maps_host;
+  for (int k = 0; k < kOzSlices; ++k)
+    if (tc_encode_map(&m[k], it.oz_sl[k], it.Mp, 0, err, errlen, BK)) return 1;
+  const void* halves[4] = {it.oz_dh, it.oz_dl, it.oz_xh, it.oz_xl};
+  for (int k = 0; k < 4; ++k)
+    if (tc_encode_map(&m[kOzSlices + k], halves[k], it.Mp, 0, err, errlen)) return 1;
+  return 0;
 }
 
 int oz_finalize_blocks(int M) { return M < 1024 ? M : 1024; }

@@ -461,7 +461,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
       c.ep.out_l = it.Sl;
       c.ah = c.bh = &maps[2 * par];
       c.al = c.bl = &maps[2 * par + 1];
-    } else {
+    } else if (MODE == 2) {
       // the control kernel flipped the parity: read par^1, write par
       c.ep.X = it.X[par ^ 1];
       c.ep.Sig = it.Sig;
@@ -472,6 +472,20 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
       c.al = &maps[2 * (par ^ 1) + 1];
       c.bh = &maps[4];
       c.bl = &maps[5];
+    } else {
+      // refinement product (X = S - D) D: the iterate just evaluated is
+      // par^1 (the control kernel flipped the parity), the step writes par
+      const CUtensorMap* om = (const CUtensorMap*)it.oz_maps;
+      c.ah = &om[kOzSlices + 2];
+      c.al = &om[kOzSlices + 3];
+      c.bh = &om[kOzSlices];
+      c.bl = &om[kOzSlices + 1];
+      c.ep.S64 = it.S64;
+      c.ep.D64 = it.D64[par ^ 1];
+      c.ep.Dn64 = it.D64[par];
+      c.ep.rs_x = it.oz_xs;
+      c.ep.rs_d = it.oz_rs;
+      c.ep.ld64 = it.M;
     }
     tc_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
   }
@@ -903,6 +917,12 @@ int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int*
   if (mode == 1)
     return bf16 ? launch_tc<1, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
                 : launch_tc<1, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
+  if (mode == 3) {
+    // refinement product: fp16 halves, scales carried by the operands
+    ep.split_scale = 1.0f;
+    ep.inv_s2 = 1.0f;
+    return launch_tc<3, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
+  }
   return bf16 ? launch_tc<2, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
               : launch_tc<2, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
 }

@@ -57,12 +57,13 @@ def test_batched_fp64_matches_oracle(solver, batch):
         assert abs(info["energy"] - ref["E"]) <= 1e-12 * abs(ref["E"])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed_fp16", "fp16x3"])
-def test_batched_equals_loop_of_single_solves(solver, batch, prec):
+@pytest.mark.parametrize("prec,refine", [("fp64", "fp64"), ("mixed_fp16", "fp64"),
+                                         ("mixed_fp16", "slices"), ("mixed_bf16", "slices"),
+                                         ("fp16x3", "fp64")])
+def test_batched_equals_loop_of_single_solves(solver, batch, prec, refine):
     Hs = [_dev(H) for H, _, _, _ in batch]
     Ns = [N for _, N, _, _ in batch]
-    # the batched mixed solve refines with FP64 products
-    kw = dict(prec=prec, tol=1e-10 if prec != "fp16x3" else 1e-12, refine="fp64")
+    kw = dict(prec=prec, tol=1e-10 if prec != "fp16x3" else 1e-12, refine=refine)
     Ds, infos = solver.solve_batched(Hs, Ns, **kw)
     for H, N, D, info in zip(Hs, Ns, Ds, infos):
         D1, i1 = solver.solve(H, N, out_dtype=D.dtype, **kw)
@@ -82,6 +83,17 @@ def test_batched_mixed_accuracy(solver, batch):
         assert abs(np.trace(Dg) - N) <= 1e-9
         assert np.linalg.norm(Dg - Dref) / np.sqrt(N) <= 3e-6
         assert abs(info["energy"] - eps[:N].sum()) <= 1e-9 * abs(eps[:N].sum())
+
+
+def test_batched_pmcp_equals_loop(solver, batch):
+    Hs = [_dev(H) for H, _, _, _ in batch[:4]]
+    Ns = [N for _, N, _, _ in batch[:4]]
+    for prec in ("fp64", "mixed_fp16"):
+        Ds, infos = solver.solve_batched(Hs, Ns, prec=prec, tol=1e-10, method="pmcp")
+        for H, N, D, info in zip(Hs, Ns, Ds, infos):
+            D1, i1 = solver.solve(H, N, out_dtype=D.dtype, prec=prec, tol=1e-10, method="pmcp")
+            assert info["iters"] == i1["iters"] and info["status"] == i1["status"] == 0
+            assert torch.equal(D, D1)
 
 
 def test_batched_edge_instances_do_not_disturb_others(solver, batch):
