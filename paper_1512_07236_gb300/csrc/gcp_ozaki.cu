@@ -73,18 +73,26 @@ static_assert(kSmemBytes + 512 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxW = kOzSlices;  // weights 0..9
 
+// Tile order: super-columns of 8 column blocks, row block by row block
+// inside each (the tiles with I < 2J + 2), so that concurrent CTAs share
+// their slice panels in L2.
 __device__ __forceinline__ void oz_tile(int t, int NI, int NJ, int& I, int& J) {
-  int j = 0;
-  while (true) {
-    const int cnt = (2 * j + 2 < NI ? 2 * j + 2 : NI);
-    if (t < cnt || j + 1 >= NJ) {
-      I = t;
-      J = j;
-      return;
+  constexpr int kGroupJ = 8;
+  for (int j0 = 0; j0 < NJ; j0 += kGroupJ) {
+    const int j1 = j0 + kGroupJ < NJ ? j0 + kGroupJ : NJ;
+    for (int i = 0; i < NI; ++i) {
+      const int jstart = (i >> 1) > j0 ? (i >> 1) : j0;
+      const int cnt = j1 > jstart ? j1 - jstart : 0;
+      if (t < cnt) {
+        I = i;
+        J = jstart + t;
+        return;
+      }
+      t -= cnt;
     }
-    t -= cnt;
-    ++j;
   }
+  I = 0;  // not reached for t < tc_num_tiles
+  J = 0;
 }
 
 // ---- slicing ---------------------------------------------------------------

@@ -109,20 +109,28 @@ struct Epi {
 };
 
 // Linear tile index -> (I, J): I a 128-row block, J a 256-column block,
-// kept when the tile reaches the upper block triangle (2J + 1 >= I).
-// Column-block-major order so that concurrent CTAs share their B panel.
+// kept when the tile reaches the upper block triangle (I < 2J + 2, i.e.
+// J >= floor(I / 2)).  Order: super-columns of kGroupJ column blocks; in
+// each, row block by row block, the super-column's tiles of that row.  The
+// CTAs working at the same time then share a few A panels (rows) and the
+// super-column's B panels, which stay in L2 while the CTAs stream along K.
+constexpr int kGroupJ = 8;
 __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
-  int j = 0;
-  while (true) {
-    const int cnt = (2 * j + 2 < NI ? 2 * j + 2 : NI);  // I in [0, min(2J+2, NI))
-    if (t < cnt || j + 1 >= NJ) {
-      I = t;
-      J = j;
-      return;
+  for (int j0 = 0; j0 < NJ; j0 += kGroupJ) {
+    const int j1 = j0 + kGroupJ < NJ ? j0 + kGroupJ : NJ;
+    for (int i = 0; i < NI; ++i) {
+      const int jstart = (i >> 1) > j0 ? (i >> 1) : j0;
+      const int cnt = j1 > jstart ? j1 - jstart : 0;
+      if (t < cnt) {
+        I = i;
+        J = jstart + t;
+        return;
+      }
+      t -= cnt;
     }
-    t -= cnt;
-    ++j;
   }
+  I = 0;  // not reached for t < tc_num_tiles
+  J = 0;
 }
 
 // Output epilogue of one thread: its row, 128 columns of one 128-block
