@@ -128,6 +128,24 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The slowest rank's time: replicas are timed each on its own GPU and the
+    whole job lasts as long as the slowest one (a MAX all-reduce)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_solve, steps, world, ms_total):
+    """Every replica solves its own H each step (weak scaling): the job's
+    rate is all ranks' work over the slowest rank's time."""
+    return world * flops_per_solve * steps / (ms_total * 1e-3) / 1e12
+
+
 def lookup_traffic(kernel, M):
     """DRAM bytes per launch of `kernel` at this M from the committed ncu
     summary table, or None when there is none or the kernel's source file
@@ -366,14 +384,11 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     iters = infos[-1]["iters"]
     flops_step = 4.0 * M ** 3 * iters
-    value = world * flops_step * args.steps / (ms_total * 1e-3) / 1e12
+    value = whole_job_tflops(flops_step, args.steps, world, ms_total)
 
     # --- accuracy of the returned D against the exact projector (FP64) ----
     acc = {}
@@ -476,7 +491,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
-    e2e_value = world * flops_step * args.steps / (ms_e2e * 1e-3) / 1e12
+    e2e_value = whole_job_tflops(flops_step, args.steps, world, max_over_ranks(ms_e2e, world, dev))
 
     # --- CPU oracle baseline on a bounded sample ---------------------------
     cpu = None
