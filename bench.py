@@ -242,7 +242,7 @@ def run_workload(args, rank):
         M, N = Hf.shape[0], Hf.shape[0] // 2
         Ht = torch.from_numpy(Hf).cuda()
         D = torch.empty((M, M), dtype=torch.float64, device="cuda")
-        opts = dict(prec=args.prec, tol=TOL)
+        opts = dict(prec=args.prec, tol=TOL, guess=args.guess, method=args.method)
         for _ in range(W):
             solver.solve(Ht, N, out=D, **opts)
         with ClockSampler(0) as clk:
@@ -253,14 +253,15 @@ def run_workload(args, rank):
         R = float(torch.linalg.norm(D @ D - D))
         fp64_ms = None
         if not args.skip_fp64:
-            fp64_ms, (_, i64) = _cuda_ms(lambda: solver.solve(Ht, N, prec="fp64", tol=TOL), 1,
+            fp64_ms, (_, i64) = _cuda_ms(lambda: solver.solve(Ht, N, prec="fp64", tol=TOL,
+                                                              guess=args.guess), 1,
                                          stream)
         line.update({
             "metric": "time to ||D^2-D||_F<=1e-6, tight-binding insulator", "value": ms * 1e-3,
             "unit": "s", "higher_is_better": False, "ms_per_step": ms, "dtype": "fp16x3+f64",
             "config": {"workload": "simple-cubic 20^3 tight-binding, t=-1, onsite +-0.5, "
                                    "disorder 0.1, FP32 storage, N=4000", "M": M, "N": N,
-                       "prec": args.prec, "iters": info["iters"]},
+                       "prec": args.prec, "guess": args.guess, "iters": info["iters"]},
             "energy_err_per_site": abs(info["energy"] - E_ref) / M,
             "idem_fro": R, "trace_err": abs(float(torch.trace(D)) - N),
             "fp64_gpu_path_ms": fp64_ms,
@@ -270,7 +271,7 @@ def run_workload(args, rank):
         items = inputs.batched_rotated(512, qr_backend="torch")
         Hs = [torch.from_numpy(H).cuda() for H, _, _, _ in items]
         Ns = [N for _, N, _, _ in items]
-        opts = dict(prec=args.prec, tol=TOL)
+        opts = dict(prec=args.prec, tol=TOL, guess=args.guess, method=args.method)
         for _ in range(W):
             solver.solve_batched(Hs, Ns, **opts)
         with ClockSampler(0) as clk:
@@ -290,7 +291,7 @@ def run_workload(args, rank):
             "unit": "solves/s", "higher_is_better": True, "ms_per_step": ms,
             "dtype": "fp16x3+f64" if "mixed" in args.prec else args.prec,
             "config": {"workload": "512 rotated spectra, M in {64,96,...,1024}, N=M/4, "
-                                   "gap U[0.02,0.2]", "prec": args.prec,
+                                   "gap U[0.02,0.2]", "prec": args.prec, "guess": args.guess,
                        "sum_M2": int(sum(H.shape[0] ** 2 for H in Hs))},
             "loop_of_single_solves_per_s": 512 / (loop_ms * 1e-3),
             "speedup_vs_loop": loop_ms / ms,

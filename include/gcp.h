@@ -119,7 +119,7 @@ typedef struct {
  *                        the particle-hole duality of the recursion.  Its
  *                        spectrum leaves [0, 1] away from half filling,
  *                        where the solve reports GCP_ERR_ILL_CONDITIONED.
- * gcp_solve_batched and gcp_backward take GCP_GUESS_CANONICAL only. */
+ * gcp_backward takes GCP_GUESS_CANONICAL only. */
 typedef enum {
   GCP_GUESS_CANONICAL = 0,
   GCP_GUESS_HPCP_PLUS = 1,

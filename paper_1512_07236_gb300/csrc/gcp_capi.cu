@@ -761,8 +761,6 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || o.history_cap != 0)
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad arguments");
   if (!valid_modes(o)) return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad guess or method");
-  if (o.guess != GCP_GUESS_CANONICAL)
-    return fail(h, GCP_ERR_UNSUPPORTED, "gcp_solve_batched: canonical guess only");
   for (int b = 0; b < batch; ++b)
     if (!H[b] || !D_out[b] || M[b] <= 0 || N[b] < 0 || N[b] > M[b] || ld[b] < M[b])
       return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad instance %d", b);
@@ -1062,7 +1060,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   };
   auto record = [&](cudaStream_t ss, bool graph) -> gcp_status {
     launch_batch_guess(items_d, nb, maxM, h64, split ? 1 : 0, bf16, kSplitScale, gpart, gstride,
-                       ss);
+                       o.guess, ss);
     launch_batch_state_init(items_d, nb, split ? 1 : 0, ss);
     CK(cudaPeekAtLastError());
     gcp_status rr;

@@ -303,20 +303,46 @@ __global__ void __launch_bounds__(kGuessThreads) batch_guess_reduce_kernel(
                       gpart + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kGuessFields);
 }
 
-__global__ void batch_guess_finalize_kernel(const BatchItem* items, int batch,
-                                            const double* __restrict__ gpart, int gstride) {
-  const int bi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (bi >= batch) return;
-  const BatchItem& it = items[bi];
-  double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0;
-  for (int k = 0; k < it.gblocks; ++k) {
-    const double* p = gpart + ((size_t)bi * gstride + k) * kGuessFields;
-    lo = fmin(lo, p[0]);
-    hi = fmax(hi, p[1]);
-    tr += p[2];
-    mx = fmax(mx, p[3]);
+// One block per instance: the same combination as a single solve's
+// guess_finalize_kernel (partials in block order, the HPCP+ diagonal sum
+// as a block reduction), so both give the same coefficients.
+template <typename T>
+__global__ void __launch_bounds__(kGuessThreads) batch_guess_finalize_kernel(
+    const BatchItem* items, const double* __restrict__ gpart, int gstride, int mode) {
+  const BatchItem& it = items[blockIdx.x];
+  __shared__ double red[32];
+  __shared__ double mu_sh;
+  __shared__ double acc[kGuessFields];
+  if (threadIdx.x == 0) {
+    double lo = INFINITY, hi = -INFINITY, tr = 0.0, mx = 0.0, off2 = 0.0;
+    for (int k = 0; k < it.gblocks; ++k) {
+      const double* p = gpart + ((size_t)blockIdx.x * gstride + k) * kGuessFields;
+      lo = fmin(lo, p[0]);
+      hi = fmax(hi, p[1]);
+      tr += p[2];
+      mx = fmax(mx, p[3]);
+      off2 += p[4];
+    }
+    acc[0] = lo;
+    acc[1] = hi;
+    acc[2] = tr;
+    acc[3] = mx;
+    acc[4] = off2;
+    mu_sh = tr / (double)it.M;
   }
-  guess_params(lo, hi, tr, mx, 0.0, it.M, it.N, GCP_GUESS_CANONICAL, it.st);
+  __syncthreads();
+  double v[1] = {0.0};
+  if (mode == GCP_GUESS_HPCP_PLUS) {
+    const T* H = (const T*)it.H;
+    const double mu = mu_sh;
+    for (int i = threadIdx.x; i < it.M; i += blockDim.x) {
+      const double d = (double)H[(size_t)i * it.ld + i] - mu;
+      v[0] += d * d;
+    }
+  }
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0)
+    guess_params(acc[0], acc[1], acc[2], acc[3], acc[4] + v[0], it.M, it.N, mode, it.st);
 }
 
 template <typename T, bool BF16>
@@ -359,13 +385,19 @@ __global__ void batch_guess_write_d_kernel(const BatchItem* items) {
 }  // namespace
 
 void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, int split,
-                        int bf16, float split_scale, double* gpart, int gstride, cudaStream_t s) {
+                        int bf16, float split_scale, double* gpart, int gstride, int guess_mode,
+                        cudaStream_t s) {
   dim3 gr(gstride, batch);
   if (h_f64)
     batch_guess_reduce_kernel<double><<<gr, kGuessThreads, 0, s>>>(items, gpart);
   else
     batch_guess_reduce_kernel<float><<<gr, kGuessThreads, 0, s>>>(items, gpart);
-  batch_guess_finalize_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, gpart, gstride);
+  if (h_f64)
+    batch_guess_finalize_kernel<double><<<batch, kGuessThreads, 0, s>>>(items, gpart, gstride,
+                                                                        guess_mode);
+  else
+    batch_guess_finalize_kernel<float><<<batch, kGuessThreads, 0, s>>>(items, gpart, gstride,
+                                                                       guess_mode);
   if (split) {
     const int maxMp = ((maxM + 255) / 256) * 256;
     dim3 g((maxMp + 255) / 256 < 4 ? (maxMp + 255) / 256 : 4, maxMp, batch);

@@ -216,7 +216,8 @@ void adjoint_free(void* ws);
 // per instance in `gpart`, the instance using its own gblocks of them, in
 // the same order as a single solve), parameters into each State, then D0/X0.
 void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, int split,
-                        int bf16, float split_scale, double* gpart, int gstride, cudaStream_t s);
+                        int bf16, float split_scale, double* gpart, int gstride, int guess_mode,
+                        cudaStream_t s);
 void launch_batch_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
                           cudaStream_t s);
 void launch_batch_any_active(const BatchItem* items, int batch, unsigned long long cond,

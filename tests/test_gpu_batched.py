@@ -96,6 +96,24 @@ def test_batched_pmcp_equals_loop(solver, batch):
             assert torch.equal(D, D1)
 
 
+@pytest.mark.parametrize("guess", ["hpcp+", "hole"])
+def test_batched_guesses_equal_loop(solver, batch, guess):
+    """HPCP+ (Eq. hpcpguess) and hole guesses in a batch: the same
+    coefficients, steps and results as single solves (the hole guess may be
+    ill-conditioned at theta = 1/4; the status must then agree too)."""
+    Hs = [_dev(H) for H, _, _, _ in batch[:5]]
+    Ns = [N for _, N, _, _ in batch[:5]]
+    for prec in ("fp64", "mixed_fp16"):
+        Ds, infos = solver.solve_batched(Hs, Ns, prec=prec, tol=1e-10, guess=guess)
+        for H, N, D, info in zip(Hs, Ns, Ds, infos):
+            D1, i1 = solver.solve(H, N, out_dtype=D.dtype, prec=prec, tol=1e-10, guess=guess)
+            assert info["status"] == i1["status"]
+            assert info["alpha"] == i1["alpha"] and info["beta2"] == i1["beta2"]
+            if i1["status"] == 0:
+                assert info["iters"] == i1["iters"]
+                assert torch.equal(D, D1)
+
+
 def test_batched_edge_instances_do_not_disturb_others(solver, batch):
     """N = 0, N = M and H = mu I inside a batch: each gets its own status;
     the others are unaffected."""
