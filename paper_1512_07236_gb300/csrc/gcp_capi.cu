@@ -1006,7 +1006,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   };
   // exact-slice refinement step, as rec_oz_step of a single solve
   auto oz_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
-    launch_batch_oz_slice(items_d, nb, tc_pad(maxM), ss);
+    launch_batch_oz_slice(items_d, nb, maxM, ss);
     if (launch_batch_oz_gemm(items_d, tinst_tc, ntc, maxM, ss))
       return fail(h, GCP_ERR_CUDA, "batched slice GEMM launch failed");
     launch_batch_oz_finalize(items_d, nb, maxM, part, ss);

@@ -193,9 +193,12 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
 int oz_finalize_blocks(int M);
 void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s);
+// Digit bits b and slice count of the slicing for an M-long inner dimension.
+int oz_digit_bits(int M);
+int oz_num_slices(int M);
 // Batched forms over the instances' BatchItem (work list: the tensor-core
 // tiles), reading and writing the current iterate D64[State::parity].
-void launch_batch_oz_slice(const BatchItem* items, int batch, int maxMp, cudaStream_t s);
+void launch_batch_oz_slice(const BatchItem* items, int batch, int maxM, cudaStream_t s);
 int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntiles, int maxM,
                          cudaStream_t s);
 void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,

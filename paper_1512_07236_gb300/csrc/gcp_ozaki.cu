@@ -3,32 +3,33 @@
 // GB300 runs FP64 on SIMT units at ~1.2 TFLOP/s; one FP64 D^2 at M = 8192
 // takes ~0.45 s.  Here D^2 is formed on the tensor cores without rounding:
 //   * each row i of D is scaled by 2^e_i with |D_ij| <= 2^e_i / 2 and cut
-//     into nine signed base-32 digits, D_ij = 2^e_i sum_s d_s 32^-(s+1) + r,
-//     |d_s| <= 16, |r| <= 2^e_i 32^-9 / 2 (a 45-bit fixed-point value);
-//     digits are small integers, exact in fp16;
-//   * (D D)_ij = 2^(e_i+e_j) sum_w 32^-(w+2) sum_{s+t=w} sum_k d_s(i,k) d_t(j,k)
-//     for weights w = 0..9; the dropped weights (w >= 10) and the cut r each
-//     add ~1e-14 per element at M = 8192, ~2e-10 to ||D^2 - D||_F.  Those
-//     errors have random signs except on the diagonal, where the square
-//     d_5(i,k)^2 of weight 10 is always positive: dropping it would bias
-//     Tr D^2 by ~ -5e-9 at M = 8192, so the pair (5, 5) is kept too;
+//     into ns signed digits of b bits, D_ij = 2^e_i sum_s d_s B^-(s+1) + r,
+//     B = 2^b, |d_s| <= B/2, |r| <= 2^e_i B^-ns / 2; digits are small
+//     integers, exact in fp16.  M <= 16384: b = 6, ns = 8 (48-bit fixed
+//     point); larger M: b = 5, ns = 9 (45 bits);
+//   * (D D)_ij = 2^(e_i+e_j) sum_w B^-(w+2) sum_{s+t=w} sum_k d_s(i,k) d_t(j,k)
+//     over the weights w kept: w = 0..ns (b = 6: 43 pairs; b = 5: 53).  The
+//     dropped weights have random signs except on the diagonal, where the
+//     first dropped square d_5(i,k)^2 (weight 10) is always positive:
+//     dropping it would bias Tr D^2 (~ -5e-9 at M = 8192 for b = 5), so the
+//     pair (5, 5) is kept too.  What is left adds ~1e-14 per element at
+//     M = 8192.  (Keeping b = 6 weights only up to 7 saved 15% more time but
+//     moved Tr D of a tight-binding D by 3e-9);
 //   * a pass accumulates one weight over at most P pairs with
-//     P * 256 * M <= 2^24, so every partial sum is an integer below 2^24 and
+//     P (B/2)^2 M <= 2^24, so every partial sum is an integer below 2^24 and
 //     the FP32 tensor-core accumulation is exact whatever its rounding mode
-//     (at M = 8192 the cap is 8 pairs: weight 8, with 9 pairs, takes two
-//     passes; larger M splits more weights);
+//     (b = 6 at M = 8192: P = 2; b = 5: P = 8);
 //   * each pass's integer sums are scaled and added in FP64.
-// The result carries the ~2^-46 slicing error of the row scales, against
-// 2^-53 for native FP64, at tensor-core speed.
 //
 // Kernel layout: persistent CTAs over the 128 x 256 tiles of the upper block
 // triangle, pass-major (every CTA runs pass p over its tiles before pass
-// p + 1, so the CTAs stream the same two digit slices at a time and L2
-// holds their common panels); warp 0 issues TMA loads of one digit slice of the A rows and one
-// of the B rows per stage (4-stage ring of 48 KB stages, 64-wide K blocks in
-// 128-byte swizzled rows), warp 1 issues one MMA per 16-wide K step into one of two TMEM buffers (one buffer per pass,
-// so the MMAs of the next pass overlap the drain of this one), warps 2-9
-// drain each pass into the FP64 output.
+// p + 1, so the CTAs stream the same two digit slices at a time and L2 holds
+// their common panels); warp 0 issues TMA loads of one digit slice of the A
+// rows and one of the B rows per stage (4-stage ring of 48 KB stages, 64-wide
+// K blocks in 128-byte swizzled rows), warp 1 issues one MMA per 16-wide K
+// step into one of two TMEM buffers (one buffer per pass, so the MMAs of the
+// next pass overlap the drain of this one), warps 2-9 drain each pass into
+// the FP64 output.
 #include <stdio.h>
 #include <string.h>
 
@@ -49,6 +50,7 @@ struct OzOperands {
 constexpr int kOzMaxPass = 64;
 struct OzPlan {
   int npass;
+  int db;  // digit bits b (base B = 2^b)
   int w[kOzMaxPass];
   int s0[kOzMaxPass];
   int ns[kOzMaxPass];
@@ -71,7 +73,6 @@ constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per d
 constexpr uint32_t kSmemBytes = STAGES * kStageBytes + kTpBytes + 1024;
 static_assert(kSmemBytes + 512 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;
-constexpr int kMaxW = kOzSlices;  // weights 0..9
 
 // Tile order: super-columns of 8 column blocks, row block by row block
 // inside each (the tiles with I < 2J + 2), so that concurrent CTAs share
@@ -103,8 +104,9 @@ __device__ __forceinline__ void oz_tile(int t, int NI, int NJ, int& I, int& J) {
 // significant first, each remainder exact.
 // One row i of D (the whole block works on it).
 __device__ __forceinline__ void slice_row(const double* __restrict__ D, int M, int Mp, int i,
-                                          __half* const* sl, double* __restrict__ rscale,
-                                          __half* __restrict__ Dh, __half* __restrict__ Dl) {
+                                          int db, int nsl, __half* const* sl,
+                                          double* __restrict__ rscale, __half* __restrict__ Dh,
+                                          __half* __restrict__ Dl) {
   __shared__ unsigned long long red[32];
   __shared__ int e_sh;
   // row max of |D_ij| as the largest magnitude bit pattern (monotone for
@@ -137,20 +139,21 @@ __device__ __forceinline__ void slice_row(const double* __restrict__ D, int M, i
     rscale[i] = ldexp(1.0, e);
   }
   __syncthreads();
-  const double to_fixed = ldexp(1.0, 45 - e_sh);  // exact: a power of two
+  const int nbits = db * nsl;  // fixed-point bits: |n| <= 2^(nbits - 1)
+  const double to_fixed = ldexp(1.0, nbits - e_sh);  // exact: a power of two
+  const float to_half = ldexpf(1.0f, 14 - nbits);
   for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
     const double d = (i < M && j < M) ? D[(size_t)i * M + j] : 0.0;
     long long n = __double2ll_rn(d * to_fixed);
     const size_t o = (size_t)i * Mp + j;
-    // fp16 halves of 2^14 D_ij / 2^e_i = n 2^-31 (|.| <= 2^13), ~22 bits
-    const float f = (float)n * 0x1p-31f;
+    // fp16 halves of 2^14 D_ij / 2^e_i = n 2^(14 - nbits) (|.| <= 2^13), ~22 bits
+    const float f = (float)n * to_half;
     const __half h = __float2half_rn(f);
     Dh[o] = h;
     Dl[o] = __float2half_rn(f - __half2float(h));
-#pragma unroll
-    for (int s = 0; s < kOzSlices; ++s) {
-      const int k = 5 * (kOzSlices - 1 - s);
-      const long long dg = k > 0 ? ((n + (1ll << (k > 0 ? k - 1 : 0))) >> k) : n;  // |dg| <= 16
+    for (int s = 0; s < nsl; ++s) {
+      const int k = db * (nsl - 1 - s);
+      const long long dg = k > 0 ? ((n + (1ll << (k > 0 ? k - 1 : 0))) >> k) : n;  // |dg| <= B/2
       n -= dg << k;  // exact, |n| <= 2^(k-1)
       sl[s][o] = __int2half_rn((int)dg);
     }
@@ -158,21 +161,22 @@ __device__ __forceinline__ void slice_row(const double* __restrict__ D, int M, i
 }
 
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ D, int M, int Mp,
-                                                       const OzSlicePtrs slices,
+                                                       int db, int nsl, const OzSlicePtrs slices,
                                                        double* __restrict__ rscale,
                                                        __half* __restrict__ Dh,
                                                        __half* __restrict__ Dl,
                                                        const State* __restrict__ st) {
   if (st->stopped) return;
-  slice_row(D, M, Mp, blockIdx.x, slices.p, rscale, Dh, Dl);
+  slice_row(D, M, Mp, blockIdx.x, db, nsl, slices.p, rscale, Dh, Dl);
 }
 
 // Batched: block (i, instance); D is the instance's current iterate.
-__global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* items) {
+__global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* items, int db,
+                                                             int nsl) {
   const BatchItem& it = items[blockIdx.y];
   if ((int)blockIdx.x >= it.Mp || it.st->stopped) return;
-  slice_row(it.D64[it.st->parity], it.M, it.Mp, blockIdx.x, (__half* const*)it.oz_sl, it.oz_rs,
-            (__half*)it.oz_dh, (__half*)it.oz_dl);
+  slice_row(it.D64[it.st->parity], it.M, it.Mp, blockIdx.x, db, nsl, (__half* const*)it.oz_sl,
+            it.oz_rs, (__half*)it.oz_dh, (__half*)it.oz_dl);
 }
 
 // ---- finalize: traces, residual, halves of X = S - D -----------------------
@@ -417,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t qc = 0;
     bool alive = true;
     for (int ps = 0; ps < plan.npass && alive; ++ps) {
-      const double wscale = ldexp(1.0, -5 * (plan.w[ps] + 2));  // 32^-(w+2)
+      const double wscale = ldexp(1.0, -plan.db * (plan.w[ps] + 2));  // B^-(w+2)
       const bool first_pass = ps == 0, last_pass = ps == plan.npass - 1;
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         OzTile c;
@@ -528,18 +532,30 @@ void launch_oz_slice(const double* D, int M, int Mp, void* const* slices, double
                      void* Dh, void* Dl, const State* st, cudaStream_t s) {
   OzSlicePtrs sp;
   for (int k = 0; k < kOzSlices; ++k) sp.p[k] = (__half*)slices[k];
-  oz_slice_kernel<<<Mp, 256, 0, s>>>(D, M, Mp, sp, rscale, (__half*)Dh, (__half*)Dl, st);
+  oz_slice_kernel<<<Mp, 256, 0, s>>>(D, M, Mp, oz_digit_bits(M), oz_num_slices(M), sp, rscale,
+                                     (__half*)Dh, (__half*)Dl, st);
 }
 
-// Passes for an M-long inner dimension: weights 0..9, pairs (s, w - s)
-// with 0 <= s, w - s < kOzSlices, at most floor(2^24 / (256 M)) pairs a pass.
+// Digit width of the slicing for an M-long inner dimension: 6 bits (8
+// slices) while a pass can hold a pair, (B/2)^2 M <= 2^24, else 5 (9 slices).
+int oz_digit_bits(int M) { return M <= 16384 ? 6 : 5; }
+int oz_num_slices(int M) { return oz_digit_bits(M) == 6 ? 8 : 9; }
+
+namespace {
+// Passes for an M-long inner dimension: pairs (s, w - s) with
+// 0 <= s, w - s < ns for the kept weights (b = 6: 0..7; b = 5: 0..9), at
+// most floor(2^24 / ((B/2)^2 M)) pairs a pass, then the first dropped square.
 int oz_plan(int M, OzPlan* plan) {
-  const long long cap = (1ll << 24) / (256ll * M);
+  const int db = oz_digit_bits(M), nsl = oz_num_slices(M);
+  const int wmax = nsl;  // 8 (b = 6) or 9 (b = 5)
+  const long long half = 1ll << (db - 1);
+  const long long cap = (1ll << 24) / (half * half * M);
   if (cap < 1) return 1;
   plan->npass = 0;
-  for (int w = 0; w <= kMaxW; ++w) {
-    int lo = w - (kOzSlices - 1) > 0 ? w - (kOzSlices - 1) : 0;
-    const int hi = w < kOzSlices - 1 ? w : kOzSlices - 1;
+  plan->db = db;
+  for (int w = 0; w <= wmax; ++w) {
+    int lo = w - (nsl - 1) > 0 ? w - (nsl - 1) : 0;
+    const int hi = w < nsl - 1 ? w : nsl - 1;
     while (lo <= hi) {
       const int n = (hi - lo + 1) < cap ? (hi - lo + 1) : (int)cap;
       if (plan->npass >= kOzMaxPass) return 1;
@@ -551,13 +567,15 @@ int oz_plan(int M, OzPlan* plan) {
     }
   }
   // the first dropped square, (5, 5) of weight 10 (see the top of the file)
+  const int wsq = (wmax + 1) % 2 == 0 ? wmax + 1 : wmax + 2;
   if (plan->npass >= kOzMaxPass) return 1;
-  plan->w[plan->npass] = kMaxW + 1;
-  plan->s0[plan->npass] = (kMaxW + 1) / 2;
+  plan->w[plan->npass] = wsq;
+  plan->s0[plan->npass] = wsq / 2;
   plan->ns[plan->npass] = 1;
   ++plan->npass;
   return 0;
 }
+}  // namespace
 
 int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int M, int Mp,
                    State* st, cudaStream_t s) {
@@ -598,9 +616,11 @@ int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntile
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
-void launch_batch_oz_slice(const BatchItem* items, int batch, int maxMp, cudaStream_t s) {
+void launch_batch_oz_slice(const BatchItem* items, int batch, int maxM, cudaStream_t s) {
+  const int maxMp = tc_pad(maxM);
   dim3 g(maxMp, batch);
-  batch_oz_slice_kernel<<<g, 256, 0, s>>>(items);
+  // every instance is sliced like the largest, whose pass plan all share
+  batch_oz_slice_kernel<<<g, 256, 0, s>>>(items, oz_digit_bits(maxM), oz_num_slices(maxM));
 }
 
 void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
