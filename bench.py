@@ -409,9 +409,10 @@ def main():
     # --- the products, each timed alone with CUDA events ------------------
     # Per launch, algorithmic work = one dense-equivalent product, 2 M^3.
     # Executed tensor work counts the computed 128 x 256 upper tiles: 3
-    # products for a split GEMM, 54 digit-slice pairs for the exact D^2 (the
-    # 53 pairs of weights 0..9 of nine slices plus the (5, 5) square), 3 for
-    # the refinement's (D^2 - D) D.
+    # products for a split GEMM, the digit-slice pairs for the exact D^2 (up
+    # to M = 16384: the 43 pairs of weights 0..8 of eight base-64 slices plus
+    # the (5, 5) square; beyond: 53 pairs of nine base-32 slices plus the
+    # square), 3 for the refinement's (D^2 - D) D.
     split_prec = "bf16x3" if "bf16" in args.prec else "fp16x3"
     peaks = {}
     try:
@@ -443,7 +444,7 @@ def main():
                 "what": "exact digit-slice D^2 of one refinement step", "ms": o1,
                 "launches_per_solve": l64 + 1, "ms_per_solve": o1 * (l64 + 1),
                 "achieved_tflops": alg / (o1 * 1e-3) / 1e12,
-                "executed_tflops": 54 * tile_flops / (o1 * 1e-3) / 1e12}
+                "executed_tflops": (44 if M <= 16384 else 54) * tile_flops / (o1 * 1e-3) / 1e12}
             kern["tc_gemm_kernel<3>"] = {
                 "what": "refinement product (D^2 - D) D", "ms": o2, "launches_per_solve": l64,
                 "ms_per_solve": o2 * l64, "executed_tflops": 3 * tile_flops / (o2 * 1e-3) / 1e12}
