@@ -12,7 +12,9 @@
 //   * c_0 outside [0,1] reports GCP_ERR_ILL_CONDITIONED (Eqs. pmcpcons2-3);
 //   * FP64 stagnation: once R < 1e-8, two consecutive non-decreasing R;
 //   * split-precision floor: once R < 1e-2, a step that fails to reduce R
-//     by 4x ends the split phase (the products can go no further).
+//     by 4x ends the split phase (the products can go no further);
+//   * mixed modes with the ||D^2 - D||_F test: the split phase also ends
+//     once R <= sqrt(tol/3)/2, from where one refinement step suffices.
 #include "gcp_device.cuh"
 #include "gcp_internal.cuh"
 
@@ -130,6 +132,13 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       status = (R <= ctl.tol) ? GCP_OK : GCP_ERR_NOT_CONVERGED;
     } else if (ctl.phase == 1 && R < 1e-2 && R > 0.25 * st->Rp0) {
       // the split products can go no further: the residual stalls
+      stop = 1;
+      kind = 2;
+    } else if (ctl.phase == 1 && !ctl.final_phase && ctl.stop == GCP_STOP_IDEMP_FRO &&
+               R <= 0.5 * sqrt(ctl.tol / 3.0)) {
+      // mixed modes: one McWeeny step of the refinement takes R to ~3 R^2,
+      // below tol/12 from here, so the split phase hands over now instead of
+      // running on to its floor
       stop = 1;
       kind = 2;
     } else if (n >= ctl.max_iter) {
