@@ -36,10 +36,14 @@
 //          (= 2 theta (1-theta)(theta - c) for HPCP).
 //
 // Schedule.  Persistent CTAs (one per SM) walk the 128 x 256 tiles of the
-// upper block triangle.  Warp 0 lane 0 issues TMA loads (SWIZZLE_64B,
-// 32-wide K blocks, a 4-stage ring of 48 KB stages), warp 1 lane 0 issues
-// tcgen05.mma, warps 2-9 drain TMEM and run the epilogue (warp w reads TMEM
-// lanes 32(w%4).. and columns 128((w-2)/4)..).  Blocks below the diagonal
+// upper block triangle.  Three warpgroups: in the first, warp 0 lane 0
+// issues TMA loads (SWIZZLE_64B, 32-wide K blocks, a 4-stage ring of 48 KB
+// stages) and warp 1 lane 0 issues tcgen05.mma (warps 2-3 idle); warps
+// 4-11 drain TMEM and run the epilogue (warp w reads TMEM lanes 32(w%4)..
+// and columns 128((w-4)/4)..).  The first warpgroup hands registers to the
+// other two (setmaxnreg: 40 and 232 a thread against 168 at launch), which
+// hold the 128 x 256 FP32 accumulator, 128 values a thread, without
+// spilling.  Blocks below the diagonal
 // inside a tile are skipped in the epilogue; every element above the
 // diagonal is stored twice (direct and mirrored).  Every wait is bounded
 // (2 s); on expiry the kernel records State::timeout and winds down, still
@@ -71,7 +75,9 @@ template <int MODE>
 __host__ __device__ constexpr int kc_stages() {
   return MODE == 3 ? 1 : 4;
 }
-constexpr int kThreads = 320;
+constexpr int kThreads = 384;
+constexpr uint32_t kCtlRegs = 40, kDrainRegs = 232;  // per thread, after setmaxnreg
+static_assert(128 * kCtlRegs + 256 * kDrainRegs <= 65536, "register split");
 constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
@@ -133,162 +139,44 @@ __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
   J = 0;
 }
 
-// Output epilogue of one thread: its row, 128 columns of one 128-block
-// (jb = 2J + half), values acc[] = s^2 (A B)_row,c.
-template <int MODE, bool BF16>
-__device__ __forceinline__ void epilogue_row(const Epi& ep, int row, int c_base, bool diag_blk,
-                                             const float (&acc)[128], bool mma_valid,
-                                             float ca, float cb, float cj, float cz,
-                                             double (&dpart)[5]) {
-  using HT = typename Split<BF16>::T;
-  if constexpr (MODE == 3) {
-    // McWeeny refinement step in FP64 (Eq. mcweeny3): with S = D^2 exact
-    // and X = S - D small, 3D^2 - 2D^3 = S - 2 X D; the product Z = X D only
-    // needs the relative accuracy of the split product because |X| is small.
-    // The general step of Eq. hpcp3 is the same plus (1 - 2c)(D - S); the
-    // control kernel sets c within 1/2 +- 0.05 to put Tr D+ back at N.
-    if (row >= ep.M) return;
-    const double wr = 1.0 / (kRefScale * ep.rs_x[row]);  // powers of two: exact
-    const double g = ep.st->a;
+// Refinement-product epilogue of one thread: its row, 128 columns of one
+// 128-block (jb = 2J + half), values acc[] = (A B)_row,c in the slice scale.
+// McWeeny refinement step in FP64 (Eq. mcweeny3): with S = D^2 exact and
+// X = S - D small, 3D^2 - 2D^3 = S - 2 X D; the product Z = X D only needs
+// the relative accuracy of the split product because |X| is small.  The
+// general step of Eq. hpcp3 is the same plus (1 - 2c)(D - S); the control
+// kernel sets c within 1/2 +- 0.05 to put Tr D+ back at N.
+__device__ __forceinline__ void refine_row(const Epi& ep, int row, int c_base, bool diag_blk,
+                                           const float (&acc)[128]) {
+  if (row >= ep.M) return;
+  const double wr = 1.0 / (kRefScale * ep.rs_x[row]);  // powers of two: exact
+  const double g = ep.st->a;
 #pragma unroll
-    for (int k = 0; k < 128; ++k) {
-      const int c = c_base + k;
-      if (c >= ep.M || (diag_blk && c < row)) continue;
-      const size_t o = (size_t)row * ep.ld64 + c;
-      const double sv = ep.S64[o];
-      const double v = sv - 2.0 * (wr * ep.rs_d[c]) * (double)acc[k] - g * (sv - ep.D64[o]);
-      ep.Dn64[o] = v;
-      if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
-    }
-    return;
-  }
-  const int Mp = ep.Mp;
-  const double th = ep.st->theta;
-  const float f2th = (float)(2.0 * th);
-  const float thtb = (float)(th * (1.0 - th));
-  const bool in_m = row < ep.M;
-#pragma unroll
-  for (int sub = 0; sub < 8; ++sub) {
-    const int c0 = c_base + sub * 16;
-    const size_t rowoff = (size_t)row * Mp + c0;
-    float x[16], o[16];
-    {
-      const float4* px = reinterpret_cast<const float4*>(ep.X + rowoff);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 t = px[q];
-        x[4 * q] = t.x;
-        x[4 * q + 1] = t.y;
-        x[4 * q + 2] = t.z;
-        x[4 * q + 3] = t.w;
-      }
-    }
-    if (MODE == 1) {
-      float p2 = 0.f, p3 = 0.f, p4 = 0.f;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int c = c0 + k;
-        const float y = acc[sub * 16 + k] * ep.inv_s2;
-        const float sg = fmaf(f2th, x[k], y);  // Sigma = 2 theta X + Y
-        o[k] = sg;
-        // weight: an element above the diagonal stands for its mirror too;
-        // in a diagonal block only the upper triangle is kept
-        const float w = diag_blk ? (c > row ? 2.f : (c == row ? 1.f : 0.f)) : 2.f;
-        const bool on_diag = diag_blk && (c == row) && in_m;
-        const float e = sg - x[k] - (on_diag ? thtb : 0.f);  // (S - D)_ij
-        p2 = fmaf(w * sg, x[k], p2);
-        p3 = fmaf(w * e, e, p3);
-        if (on_diag) {
-          dpart[0] += (double)x[k];
-          dpart[1] += (double)sg;
-        }
-        if (ep.H && in_m && c < ep.M) {
-          const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)row * ep.ldh + c]
-                                    : (double)((const float*)ep.H)[(size_t)row * ep.ldh + c];
-          const float d = x[k] + (on_diag ? (float)th : 0.f);
-          p4 = fmaf(w * d, (float)h, p4);
-        }
-      }
-      dpart[2] += (double)p2;
-      dpart[3] += (double)p3;
-      dpart[4] += (double)p4;
-    } else {
-      float sg[16];
-      const float4* ps = reinterpret_cast<const float4*>(ep.Sig + rowoff);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 t = ps[q];
-        sg[4 * q] = t.x;
-        sg[4 * q + 1] = t.y;
-        sg[4 * q + 2] = t.z;
-        sg[4 * q + 3] = t.w;
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        if (mma_valid) {
-          const float z = acc[sub * 16 + k] * ep.inv_s2;
-          const bool on_diag = diag_blk && (c0 + k == row) && in_m;
-          o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], cz * z)) + (on_diag ? cj : 0.f);
-        } else {
-          o[k] = x[k];
-        }
-      }
-    }
-    HT h[16], l[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) Split<BF16>::split(o[k] * ep.split_scale, h[k], l[k]);
-    if (diag_blk) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int c = c0 + k;
-        if (c < row) continue;
-        const size_t d0 = (size_t)row * Mp + c, mo = (size_t)c * Mp + row;
-        ep.out[d0] = o[k];
-        reinterpret_cast<HT*>(ep.out_h)[d0] = h[k];
-        reinterpret_cast<HT*>(ep.out_l)[d0] = l[k];
-        if (c > row) {
-          ep.out[mo] = o[k];
-          reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
-          reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
-        }
-      }
-    } else {
-      float4* po = reinterpret_cast<float4*>(ep.out + rowoff);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        po[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      uint4* ph = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_h) + rowoff);
-      uint4* pl = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_l) + rowoff);
-      ph[0] = *reinterpret_cast<const uint4*>(&h[0]);
-      ph[1] = *reinterpret_cast<const uint4*>(&h[8]);
-      pl[0] = *reinterpret_cast<const uint4*>(&l[0]);
-      pl[1] = *reinterpret_cast<const uint4*>(&l[8]);
-      // mirror: element (row, c) -> (c, row); lanes hold consecutive rows,
-      // so each of these stores is one coalesced segment per warp
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const size_t mo = (size_t)(c0 + k) * Mp + row;
-        ep.out[mo] = o[k];
-        reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
-        reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
-      }
-    }
+  for (int k = 0; k < 128; ++k) {
+    const int c = c_base + k;
+    if (c >= ep.M || (diag_blk && c < row)) continue;
+    const size_t o = (size_t)row * ep.ld64 + c;
+    const double sv = ep.S64[o];
+    const double v = sv - 2.0 * (wr * ep.rs_d[c]) * (double)acc[k] - g * (sv - ep.D64[o]);
+    ep.Dn64[o] = v;
+    if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
   }
 }
 
 // GEMM1 epilogue of one warp for one 32 x 32 block: rows row0..row0+31,
 // columns c0..c0+31, v[k] = s^2 (X X)_{row0+lane, c0+k} (lane = row, as the
 // accumulator comes out of TMEM).  The block goes through the warp's shared
-// buffer `tp` (4-float groups XOR-swizzled by row: conflict-free for float4
-// and scalar access) and is read back with eight lanes per row and four
-// consecutive columns per lane, so that the X loads and the direct stores
-// of Sigma and its halves are whole 128-byte row segments; Sigma goes back
-// to `tp` and the mirrored stores read it with eight lanes per column.
+// buffer `tp` (4-float groups XOR-swizzled by row) and is read back with
+// eight lanes per row and four consecutive columns per lane, so that the X
+// loads and the direct stores of Sigma and its halves are whole 128-byte
+// row segments; Sigma goes back to `tp` and the mirrored stores read it with
+// eight lanes per column.
 // Blocks on the diagonal take an element-wise path (upper triangle only).
-// (GEMM2's epilogue keeps lane = row: there the transposes cost more than
-// the coalescing saves.)
+// The XOR key (r ^ r >> 2) & 7 takes eight distinct values over any eight
+// consecutive rows (float4 rows written by lanes = rows) and over rows
+// 4g + i, g = 0..7 (the mirrored reads): both are conflict-free.
 __device__ __forceinline__ int tp_idx(int r, int c) {
-  return r * 32 + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3));
+  return r * 32 + ((((c >> 2) ^ ((r ^ (r >> 2)) & 7)) << 2) | (c & 3));
 }
 
 template <bool BF16>
@@ -316,13 +204,10 @@ __device__ __forceinline__ void store_out1(const Epi& ep, size_t off, float o) {
 
 template <bool BF16>
 __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, bool diag_blk,
-                                            const float* v, float (&pp)[3], double (&dpart)[5],
-                                            float* tp) {
+                                            const float* v, float thf, float f2th, float thtb,
+                                            float (&pp)[3], double (&dpart)[5], float* tp) {
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
-  const double th = ep.st->theta;
-  const float f2th = (float)(2.0 * th);
-  const float thtb = (float)(th * (1.0 - th));
   const float is2 = ep.inv_s2;
 #pragma unroll
   for (int g = 0; g < 8; ++g)
@@ -333,13 +218,15 @@ __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, boo
     // every element lies above the diagonal (weight 2, mirrored)
     const int rs = lane >> 3, cl = 4 * (lane & 7);
     const size_t cbase = (size_t)c0 + cl;
+    // all eight X loads in flight before the first store (loads issued
+    // after stores queue behind them)
+    float4 xx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      xx[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(row0 + rs + 4 * j) * Mp + cbase);
 #pragma unroll
     for (int jh = 0; jh < 8; jh += 4) {
-      float4 x[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        x[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(row0 + rs + 4 * (jh + j)) * Mp +
-                                                cbase);
+      const float4* x = xx + jh;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int rr = rs + 4 * (jh + j);
@@ -406,7 +293,7 @@ __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, boo
       if (ep.H && r < ep.M && c < ep.M) {
         const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + c]
                                   : (double)((const float*)ep.H)[(size_t)r * ep.ldh + c];
-        const float d = x + (on_diag ? (float)th : 0.f);
+        const float d = x + (on_diag ? thf : 0.f);
         pp[2] += w * d * (float)h;
       }
       o[k] = sg;
@@ -424,6 +311,93 @@ __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, boo
       store_out1<BF16>(ep, (size_t)cc * Mp + r, tp[tp_idx(lane, k)]);
     }
     __syncwarp();
+  }
+}
+
+// GEMM2 epilogue of one thread: its row, 128 columns of one 128-block
+// (jb = 2J + half), acc[] = s^2 (X Sigma)_row,c;
+// X_{n+1} = ca X + cb Sigma + cz Z (+ cj on the diagonal of the unpadded
+// block); without products (mma false) a copy of X.  Lane = row: the float4
+// loads of X and Sigma stay in L1 across the row's eight 16-column steps
+// (a transposed layout as in gemm1_block measured slower here).
+template <bool BF16>
+__device__ __forceinline__ void gemm2_row(const Epi& ep, int row, int c_base, bool diag_blk,
+                                          const float (&acc)[128], bool mma, float ca, float cb,
+                                          float cj, float cz) {
+  using HT = typename Split<BF16>::T;
+  const int Mp = ep.Mp;
+  const bool in_m = row < ep.M;
+#pragma unroll
+  for (int sub = 0; sub < 8; ++sub) {
+    const int c0 = c_base + sub * 16;
+    const size_t rowoff = (size_t)row * Mp + c0;
+    float x[16], o[16], sg[16];
+    {
+      const float4* px = reinterpret_cast<const float4*>(ep.X + rowoff);
+      const float4* ps = reinterpret_cast<const float4*>(ep.Sig + rowoff);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = px[q];
+        x[4 * q] = t.x;
+        x[4 * q + 1] = t.y;
+        x[4 * q + 2] = t.z;
+        x[4 * q + 3] = t.w;
+        const float4 u = ps[q];
+        sg[4 * q] = u.x;
+        sg[4 * q + 1] = u.y;
+        sg[4 * q + 2] = u.z;
+        sg[4 * q + 3] = u.w;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (mma) {
+        const float z = acc[sub * 16 + k] * ep.inv_s2;
+        const bool on_diag = diag_blk && (c0 + k == row) && in_m;
+        o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], cz * z)) + (on_diag ? cj : 0.f);
+      } else {
+        o[k] = x[k];
+      }
+    }
+    HT h[16], l[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Split<BF16>::split(o[k] * ep.split_scale, h[k], l[k]);
+    if (diag_blk) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int c = c0 + k;
+        if (c < row) continue;
+        const size_t d0 = (size_t)row * Mp + c, mo = (size_t)c * Mp + row;
+        ep.out[d0] = o[k];
+        reinterpret_cast<HT*>(ep.out_h)[d0] = h[k];
+        reinterpret_cast<HT*>(ep.out_l)[d0] = l[k];
+        if (c > row) {
+          ep.out[mo] = o[k];
+          reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
+          reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
+        }
+      }
+    } else {
+      float4* po = reinterpret_cast<float4*>(ep.out + rowoff);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        po[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      uint4* ph = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_h) + rowoff);
+      uint4* pl = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_l) + rowoff);
+      ph[0] = *reinterpret_cast<const uint4*>(&h[0]);
+      ph[1] = *reinterpret_cast<const uint4*>(&h[8]);
+      pl[0] = *reinterpret_cast<const uint4*>(&l[0]);
+      pl[1] = *reinterpret_cast<const uint4*>(&l[8]);
+      // mirror: element (row, c) -> (c, row); lanes hold consecutive rows,
+      // so each of these stores is one coalesced segment per warp
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const size_t mo = (size_t)(c0 + k) * Mp + row;
+        ep.out[mo] = o[k];
+        reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
+        reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
+      }
+    }
   }
 }
 
@@ -527,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t acce_bar[2];
   __shared__ __align__(8) uint64_t fin_bar;
   __shared__ uint32_t tmem_holder;
-  __shared__ double red[8 * 5];
+  __shared__ double red[2 * 8 * 5];
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -556,8 +530,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_holder;
   int* timeout_flag = BATCHED ? &items[0].st->timeout : &ep.st->timeout;
 
-  if (warp == 0) {
-    if (lane == 0) {
+  if (warp < 4) {
+    reg_dealloc<kCtlRegs>();
+    if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
       uint32_t g = 0;  // global stage counter
       bool alive = true;
@@ -587,9 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t first = g > STAGES ? g - STAGES : 0;
       for (uint32_t k = first; k < g; ++k)
         if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(timeout_flag, 1);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
+    } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = idesc_f16(BF16 ? 1 : 0);
       uint32_t g = 0, qc = 0;  // global stage and chunk counters
@@ -637,13 +610,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&fin_bar, 0)) atomicOr(timeout_flag, 1);
     }
   } else {
-    // ---------------- drain + epilogue (warps 2..9) ----------------
+    reg_alloc<kDrainRegs>();
+    // ---------------- drain + epilogue (warps 4..11) ----------------
     // TMEM lane quarter is fixed by the warp's rank within its warpgroup
-    const int dw = warp - 2, q = warp & 3, half = dw >> 2;
+    const int dw = warp - 4, q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     float* tp = reinterpret_cast<float*>(smem_raw + (sbase - raw) + STAGES * kStageBytes) +
                 dw * 32 * 32;
-    uint32_t qc = 0;
+    uint32_t qc = 0, nred = 0;
     bool alive = true;
     for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
       TileCtx c;
@@ -681,42 +655,55 @@ __global__ void __launch_bounds__(kThreads, 1)
       // all drain warps agree on whether the tile completed
       drain_bar_sync();
       const bool ok = alive && !(*(volatile int*)timeout_flag);
+      // GEMM1 partials: element sums in FP32 (per lane, then a float shuffle
+      // tree), the diagonal sums Tr X, Tr Sigma in FP64 (dpart[0..1])
       double dpart[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      float pp[3] = {0.f, 0.f, 0.f};
       const int jb = 2 * c.J + half;
       if (ok && jb >= c.I) {
         if constexpr (MODE == 1) {
-          float pp[3] = {0.f, 0.f, 0.f};
+          const double th = c.ep.st->theta;
+          const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
 #pragma unroll
           for (int part = 0; part < 4; ++part)
             gemm1_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
-                              jb == c.I, &acc[part * 32], pp, dpart, tp);
-          dpart[2] += (double)pp[0];
-          dpart[3] += (double)pp[1];
-          dpart[4] += (double)pp[2];
+                              jb == c.I, &acc[part * 32], thf, f2th, thtb, pp, dpart, tp);
+        } else if constexpr (MODE == 2) {
+          gemm2_row<BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc,
+                          c.mma, c.ca, c.cb, c.cj, c.cz);
         } else {
-          epilogue_row<MODE, BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128,
-                                   jb == c.I, acc, c.mma, c.ca, c.cb, c.cj, c.cz, dpart);
+          refine_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc);
         }
       }
       if (MODE == 1) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) dpart[k] = warp_sum(dpart[k]);
+        // FP64 arithmetic is slow on this part: only warps on a diagonal
+        // block (warp-uniform) reduce the FP64 sums, and six lanes of warp
+        // 0 add the warps' rows of the table in parallel.  The table is
+        // double-buffered by the count of reduced tiles, so one barrier per
+        // tile suffices: a warp writes this buffer again only after the
+        // next tile's barrier, which warp 0 reaches after reading it.
+        const float s2 = warp_sum_f(pp[0]), s3 = warp_sum_f(pp[1]), s4 = warp_sum_f(pp[2]);
+        double d0 = 0.0, d1 = 0.0;
+        if (jb == c.I) {
+          d0 = warp_sum(dpart[0]);
+          d1 = warp_sum(dpart[1]);
+        }
+        double* r = red + (nred & 1) * 40;
         if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 5; ++k) red[dw * 5 + k] = dpart[k];
+          r[dw * 5] = d0;
+          r[dw * 5 + 1] = d1;
+          r[dw * 5 + 2] = (double)s2;
+          r[dw * 5 + 3] = (double)s3;
+          r[dw * 5 + 4] = (double)s4;
         }
         drain_bar_sync();
-        if (dw == 0 && lane == 0) {
-          double* p = ep.part + (size_t)t * kPartFields;
-#pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            double sacc = 0.0;
-            for (int w = 0; w < 8; ++w) sacc += red[w * 5 + k];
-            p[k] = sacc;
-          }
-          p[5] = 0.0;
+        if (dw == 0 && lane < kPartFields) {
+          double sacc = 0.0;
+          if (lane < 5)
+            for (int w = 0; w < 8; ++w) sacc += r[w * 5 + lane];
+          ep.part[(size_t)t * kPartFields + lane] = sacc;
         }
-        drain_bar_sync();
+        ++nred;
       }
       if (!ok) break;
     }
@@ -796,6 +783,12 @@ int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const Bat
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_bytes<MODE>());
     if (e != cudaSuccess) return 1;
+    // the register split must fit the pool the CTA is launched with, or
+    // the drain warpgroups' setmaxnreg.inc would wait forever
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<MODE, BF16, BATCHED>) != cudaSuccess ||
+        fa.numRegs * kThreads < (int)(128 * kCtlRegs + 256 * kDrainRegs))
+      return 1;
     attr = true;
   }
   const int grid = ep.ntiles < sm_count() ? ep.ntiles : sm_count();

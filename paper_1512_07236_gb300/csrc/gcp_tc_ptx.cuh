@@ -122,6 +122,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// Per-warpgroup register budgets (setmaxnreg; every thread of the warpgroup
+// executes the same one).  The increase waits until the CTA's pool, fixed
+// at launch (threads x registers per thread), has the registers: the
+// launcher checks that the budgets add up to no more than that pool.
+template <uint32_t N>
+__device__ __forceinline__ void reg_dealloc() {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <uint32_t N>
+__device__ __forceinline__ void reg_alloc() {
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
 __device__ __forceinline__ void drain_bar_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(kDrainThreads) : "memory");
 }
