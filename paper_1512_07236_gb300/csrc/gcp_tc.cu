@@ -164,13 +164,13 @@ __device__ __forceinline__ void refine_row(const Epi& ep, int row, int c_base, b
 }
 
 // GEMM1 epilogue of one warp for one 32 x 32 block: rows row0..row0+31,
-// columns c0..c0+31, v[k] = s^2 (X X)_{row0+lane, c0+k} (lane = row, as the
-// accumulator comes out of TMEM).  The block goes through the warp's shared
-// buffer `tp` (4-float groups XOR-swizzled by row) and is read back with
-// eight lanes per row and four consecutive columns per lane, so that the X
-// loads and the direct stores of Sigma and its halves are whole 128-byte
-// row segments; Sigma goes back to `tp` and the mirrored stores read it with
-// eight lanes per column.
+// columns c0..c0+31; the caller has written s^2 (X X)_{row0+lane, c0+k} to
+// row `lane` of the warp's shared buffer `tp` (lane = row, as the
+// accumulator comes out of TMEM; 4-float groups XOR-swizzled by row), and
+// the block is read back with eight lanes per row and four consecutive
+// columns per lane, so that the X loads and the direct stores of Sigma and
+// its halves are whole 128-byte row segments; Sigma goes back to `tp` and
+// the mirrored stores read it with eight lanes per column.
 // Blocks on the diagonal take an element-wise path (upper triangle only).
 // The XOR key (r ^ r >> 2) & 7 takes eight distinct values over any eight
 // consecutive rows (float4 rows written by lanes = rows) and over rows
@@ -204,15 +204,11 @@ __device__ __forceinline__ void store_out1(const Epi& ep, size_t off, float o) {
 
 template <bool BF16>
 __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, bool diag_blk,
-                                            const float* v, float thf, float f2th, float thtb,
-                                            float (&pp)[3], double (&dpart)[5], float* tp) {
+                                            float thf, float f2th, float thtb, float (&pp)[3],
+                                            double (&dpart)[5], float* tp) {
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
-#pragma unroll
-  for (int g = 0; g < 8; ++g)
-    *reinterpret_cast<float4*>(&tp[tp_idx(lane, 4 * g)]) =
-        make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
   __syncwarp();
   if (!diag_blk) {
     // every element lies above the diagonal (weight 2, mirrored)
@@ -314,6 +310,24 @@ __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, boo
   }
 }
 
+// The epilogues run once per tile, so their code is fetched cold every
+// time: each keeps one copy of its block body in a runtime loop and pulls
+// the step's accumulator registers out with these (a switch over the step
+// gives every case compile-time register indices).
+template <int P>
+__device__ __forceinline__ void acc_to_tp(const float (&acc)[128], float* tp, int lane) {
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(&tp[tp_idx(lane, 4 * g)]) =
+        make_float4(acc[32 * P + 4 * g], acc[32 * P + 4 * g + 1], acc[32 * P + 4 * g + 2],
+                    acc[32 * P + 4 * g + 3]);
+}
+template <int S>
+__device__ __forceinline__ void acc16(const float (&acc)[128], float (&z)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) z[k] = acc[16 * S + k];
+}
+
 // GEMM2 epilogue of one thread: its row, 128 columns of one 128-block
 // (jb = 2J + half), acc[] = s^2 (X Sigma)_row,c;
 // X_{n+1} = ca X + cb Sigma + cz Z (+ cj on the diagonal of the unpadded
@@ -327,8 +341,19 @@ __device__ __forceinline__ void gemm2_row(const Epi& ep, int row, int c_base, bo
   using HT = typename Split<BF16>::T;
   const int Mp = ep.Mp;
   const bool in_m = row < ep.M;
-#pragma unroll
+#pragma unroll 1
   for (int sub = 0; sub < 8; ++sub) {
+    float za[16];
+    switch (sub) {
+      case 0: acc16<0>(acc, za); break;
+      case 1: acc16<1>(acc, za); break;
+      case 2: acc16<2>(acc, za); break;
+      case 3: acc16<3>(acc, za); break;
+      case 4: acc16<4>(acc, za); break;
+      case 5: acc16<5>(acc, za); break;
+      case 6: acc16<6>(acc, za); break;
+      default: acc16<7>(acc, za); break;
+    }
     const int c0 = c_base + sub * 16;
     const size_t rowoff = (size_t)row * Mp + c0;
     float x[16], o[16], sg[16];
@@ -352,7 +377,7 @@ __device__ __forceinline__ void gemm2_row(const Epi& ep, int row, int c_base, bo
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       if (mma) {
-        const float z = acc[sub * 16 + k] * ep.inv_s2;
+        const float z = za[k] * ep.inv_s2;
         const bool on_diag = diag_blk && (c0 + k == row) && in_m;
         o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], cz * z)) + (on_diag ? cj : 0.f);
       } else {
@@ -664,10 +689,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (MODE == 1) {
           const double th = c.ep.st->theta;
           const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
-#pragma unroll
-          for (int part = 0; part < 4; ++part)
+#pragma unroll 1
+          for (int part = 0; part < 4; ++part) {
+            switch (part) {
+              case 0: acc_to_tp<0>(acc, tp, lane); break;
+              case 1: acc_to_tp<1>(acc, tp, lane); break;
+              case 2: acc_to_tp<2>(acc, tp, lane); break;
+              default: acc_to_tp<3>(acc, tp, lane); break;
+            }
             gemm1_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
-                              jb == c.I, &acc[part * 32], thf, f2th, thtb, pp, dpart, tp);
+                              jb == c.I, thf, f2th, thtb, pp, dpart, tp);
+          }
         } else if constexpr (MODE == 2) {
           gemm2_row<BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc,
                           c.mma, c.ca, c.cb, c.cj, c.cz);
