@@ -182,7 +182,14 @@ __global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* it
 // ---- finalize: traces, residual, halves of X = S - D -----------------------
 // Row i of X is scaled by xscale_i = 2^(13 - e) with max_j |X_ij| < 2^e, so
 // that its fp16 halves keep ~22 bits of every row whatever the size of X.
+// FP64 is slow on this part, so it is kept where the arithmetic needs it:
+// X = S - D (S and D are O(1), X is small), sum S o D (Tr D^3, which the
+// coefficient takes differences of) and the diagonal sums.  X itself has
+// 24 bits to spare in FP32, which holds the residual ||X||_F^2 (per lane,
+// then FP64 across lanes), the row maximum and the halves; a thread keeps
+// its first kFinCache values of the row in registers between the passes.
 constexpr int kFinThreads = 256;
+constexpr int kFinCache = 32;
 // Block `blk` of `nblk`: rows blk, blk + nblk, ...; partials into part[0..5].
 __device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
                                               const double* __restrict__ D, int M, int Mp,
@@ -190,44 +197,74 @@ __device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
                                               __half* __restrict__ Xh, __half* __restrict__ Xl,
                                               double* __restrict__ xscale) {
   __shared__ double red[32 * 5];
-  __shared__ double mred[32];
-  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  __shared__ float mred[32];
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;  // Tr D, Tr S, sum S o D
+  float v3 = 0.f;                       // ||S - D||_F^2
   for (int i = blk; i < Mp; i += nblk) {
-    double mx = 0.0;
-    if (i < M)
-      for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const size_t o = (size_t)i * M + j;
-        const double sv = S[o], dv = D[o];
-        const double x = sv - dv;
-        if (i == j) {
-          v[0] += dv;
-          v[1] += sv;
-        }
-        v[2] += sv * dv;
-        v[3] += x * x;
-        mx = fmax(mx, fabs(x));
-      }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    double m = 0.0;
-    for (int w = 0; w < kFinThreads / 32; ++w) m = fmax(m, mred[w]);
-    __syncthreads();  // mred is reused by the next row
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);  // m < 2^e
-    const double sx = ldexp(1.0, 13 - e);
-    if (threadIdx.x == 0) xscale[i] = sx;
-    for (int j = threadIdx.x; j < Mp; j += blockDim.x) {
-      double x = 0.0;
+    float xc[kFinCache];
+    float mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < kFinCache; ++k) {
+      const int j = threadIdx.x + k * kFinThreads;
+      xc[k] = 0.f;
       if (i < M && j < M) {
         const size_t o = (size_t)i * M + j;
-        x = (S[o] - D[o]) * sx;
+        const double sv = S[o], dv = D[o];
+        if (i == j) {
+          v0 += dv;
+          v1 += sv;
+        }
+        v2 += sv * dv;
+        const float x = (float)(sv - dv);
+        xc[k] = x;
+        v3 = fmaf(x, x, v3);
+        mx = fmaxf(mx, fabsf(x));
       }
-      const __half h = __double2half(x);
+    }
+    if (i < M)
+      for (int j = threadIdx.x + kFinCache * kFinThreads; j < M; j += kFinThreads) {
+        const size_t o = (size_t)i * M + j;
+        const double sv = S[o], dv = D[o];
+        if (i == j) {
+          v0 += dv;
+          v1 += sv;
+        }
+        v2 += sv * dv;
+        const float x = (float)(sv - dv);
+        v3 = fmaf(x, x, v3);
+        mx = fmaxf(mx, fabsf(x));
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    float m = 0.f;
+    for (int w = 0; w < kFinThreads / 32; ++w) m = fmaxf(m, mred[w]);
+    __syncthreads();  // mred is reused by the next row
+    int e = 0;
+    if (m > 0.f) frexpf(m, &e);  // m < 2^e
+    const float sx = ldexpf(1.0f, 13 - e);
+    if (threadIdx.x == 0) xscale[i] = (double)sx;
+    auto put = [&](int j, float x) {
+      const float y = x * sx;  // exact: a power of two
+      const __half h = __float2half_rn(y);
       Xh[(size_t)i * Mp + j] = h;
-      Xl[(size_t)i * Mp + j] = __double2half(x - (double)__half2float(h));
+      Xl[(size_t)i * Mp + j] = __float2half_rn(y - __half2float(h));
+    };
+#pragma unroll
+    for (int k = 0; k < kFinCache; ++k) {
+      const int j = threadIdx.x + k * kFinThreads;
+      if (j < Mp) put(j, xc[k]);
+    }
+    for (int j = threadIdx.x + kFinCache * kFinThreads; j < Mp; j += kFinThreads) {
+      float x = 0.f;
+      if (i < M && j < M) {
+        const size_t o = (size_t)i * M + j;
+        x = (float)(S[o] - D[o]);
+      }
+      put(j, x);
     }
   }
+  double v[5] = {v0, v1, v2, (double)v3, 0.0};
   block_sum<5>(v, red);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 5; ++k) part[k] = v[k];
