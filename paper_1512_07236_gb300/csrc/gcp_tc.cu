@@ -82,11 +82,11 @@ constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
 constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per drain warp
-// Only GEMM1's epilogue uses the transposition buffers; the other modes keep
-// that shared memory as L1 cache for their row-wise epilogue loads.
+// The split GEMMs' epilogues use the transposition buffers; the refinement
+// product keeps that shared memory as L1 cache for its row-wise FP64 loads.
 template <int MODE>
 __host__ __device__ constexpr uint32_t smem_bytes() {
-  return STAGES * kStageBytes + (MODE == 1 ? kTpBytes : 0u) + 1024;
+  return STAGES * kStageBytes + (MODE != 3 ? kTpBytes : 0u) + 1024;
 }
 static_assert(smem_bytes<1>() + 768 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
@@ -311,9 +311,10 @@ __device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, boo
 }
 
 // The epilogues run once per tile, so their code is fetched cold every
-// time: each keeps one copy of its block body in a runtime loop and pulls
-// the step's accumulator registers out with these (a switch over the step
-// gives every case compile-time register indices).
+// time: each keeps one copy of its block body in a runtime loop over the
+// four 32-column blocks and moves the block's accumulator registers to
+// shared memory with this (a switch over the block gives every case
+// compile-time register indices).
 template <int P>
 __device__ __forceinline__ void acc_to_tp(const float (&acc)[128], float* tp, int lane) {
 #pragma unroll
@@ -322,108 +323,76 @@ __device__ __forceinline__ void acc_to_tp(const float (&acc)[128], float* tp, in
         make_float4(acc[32 * P + 4 * g], acc[32 * P + 4 * g + 1], acc[32 * P + 4 * g + 2],
                     acc[32 * P + 4 * g + 3]);
 }
-template <int S>
-__device__ __forceinline__ void acc16(const float (&acc)[128], float (&z)[16]) {
-#pragma unroll
-  for (int k = 0; k < 16; ++k) z[k] = acc[16 * S + k];
-}
-
-// GEMM2 epilogue of one thread: its row, 128 columns of one 128-block
-// (jb = 2J + half), acc[] = s^2 (X Sigma)_row,c;
-// X_{n+1} = ca X + cb Sigma + cz Z (+ cj on the diagonal of the unpadded
-// block); without products (mma false) a copy of X.  Lane = row: the float4
-// loads of X and Sigma stay in L1 across the row's eight 16-column steps
-// (a transposed layout as in gemm1_block measured slower here).
+// GEMM2 epilogue of one warp for one 32 x 32 block, laid out as in
+// gemm1_block (the caller has written s^2 (X Sigma)_{row0+lane, c0+k} to
+// row `lane` of `tp`): X_{n+1} = ca X + cb Sigma + cz Z (+ cj on the
+// diagonal of the unpadded block) is formed with eight lanes per row, so the
+// X and Sigma loads and the stores are whole row segments.  In a block of
+// the diagonal 128-block only elements on or above the diagonal are stored
+// (element-wise), those above it mirrored.  Without products (mma false)
+// the block is a copy of X.
 template <bool BF16>
-__device__ __forceinline__ void gemm2_row(const Epi& ep, int row, int c_base, bool diag_blk,
-                                          const float (&acc)[128], bool mma, float ca, float cb,
-                                          float cj, float cz) {
-  using HT = typename Split<BF16>::T;
+__device__ __forceinline__ void gemm2_block(const Epi& ep, int row0, int c0, bool diag_blk,
+                                            bool mma, float ca, float cb, float cj, float cz,
+                                            float* tp) {
+  const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
-  const bool in_m = row < ep.M;
-#pragma unroll 1
-  for (int sub = 0; sub < 8; ++sub) {
-    float za[16];
-    switch (sub) {
-      case 0: acc16<0>(acc, za); break;
-      case 1: acc16<1>(acc, za); break;
-      case 2: acc16<2>(acc, za); break;
-      case 3: acc16<3>(acc, za); break;
-      case 4: acc16<4>(acc, za); break;
-      case 5: acc16<5>(acc, za); break;
-      case 6: acc16<6>(acc, za); break;
-      default: acc16<7>(acc, za); break;
+  const float is2 = ep.inv_s2;
+  const int rs = lane >> 3, cl = 4 * (lane & 7);
+  const size_t cbase = (size_t)c0 + cl;
+  float4 xx[8], ss[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const size_t off = (size_t)(row0 + rs + 4 * j) * Mp + cbase;
+    xx[j] = *reinterpret_cast<const float4*>(ep.X + off);
+    ss[j] = *reinterpret_cast<const float4*>(ep.Sig + off);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int rr = rs + 4 * j;
+    const size_t off = (size_t)(row0 + rr) * Mp + cbase;
+    const float4 a = *reinterpret_cast<const float4*>(&tp[tp_idx(rr, cl)]);
+    float4 o = xx[j];
+    if (mma) {
+      o.x = fmaf(ca, xx[j].x, fmaf(cb, ss[j].x, cz * (a.x * is2)));
+      o.y = fmaf(ca, xx[j].y, fmaf(cb, ss[j].y, cz * (a.y * is2)));
+      o.z = fmaf(ca, xx[j].z, fmaf(cb, ss[j].z, cz * (a.z * is2)));
+      o.w = fmaf(ca, xx[j].w, fmaf(cb, ss[j].w, cz * (a.w * is2)));
     }
-    const int c0 = c_base + sub * 16;
-    const size_t rowoff = (size_t)row * Mp + c0;
-    float x[16], o[16], sg[16];
-    {
-      const float4* px = reinterpret_cast<const float4*>(ep.X + rowoff);
-      const float4* ps = reinterpret_cast<const float4*>(ep.Sig + rowoff);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 t = px[q];
-        x[4 * q] = t.x;
-        x[4 * q + 1] = t.y;
-        x[4 * q + 2] = t.z;
-        x[4 * q + 3] = t.w;
-        const float4 u = ps[q];
-        sg[4 * q] = u.x;
-        sg[4 * q + 1] = u.y;
-        sg[4 * q + 2] = u.z;
-        sg[4 * q + 3] = u.w;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      if (mma) {
-        const float z = za[k] * ep.inv_s2;
-        const bool on_diag = diag_blk && (c0 + k == row) && in_m;
-        o[k] = fmaf(ca, x[k], fmaf(cb, sg[k], cz * z)) + (on_diag ? cj : 0.f);
-      } else {
-        o[k] = x[k];
-      }
-    }
-    HT h[16], l[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) Split<BF16>::split(o[k] * ep.split_scale, h[k], l[k]);
-    if (diag_blk) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int c = c0 + k;
-        if (c < row) continue;
-        const size_t d0 = (size_t)row * Mp + c, mo = (size_t)c * Mp + row;
-        ep.out[d0] = o[k];
-        reinterpret_cast<HT*>(ep.out_h)[d0] = h[k];
-        reinterpret_cast<HT*>(ep.out_l)[d0] = l[k];
-        if (c > row) {
-          ep.out[mo] = o[k];
-          reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
-          reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
-        }
-      }
+    if (!diag_blk) {
+      store_out4<BF16>(ep, off, o);
     } else {
-      float4* po = reinterpret_cast<float4*>(ep.out + rowoff);
+      const int r = row0 + rr;
+      float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        po[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-      uint4* ph = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_h) + rowoff);
-      uint4* pl = reinterpret_cast<uint4*>(reinterpret_cast<HT*>(ep.out_l) + rowoff);
-      ph[0] = *reinterpret_cast<const uint4*>(&h[0]);
-      ph[1] = *reinterpret_cast<const uint4*>(&h[8]);
-      pl[0] = *reinterpret_cast<const uint4*>(&l[0]);
-      pl[1] = *reinterpret_cast<const uint4*>(&l[8]);
-      // mirror: element (row, c) -> (c, row); lanes hold consecutive rows,
-      // so each of these stores is one coalesced segment per warp
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const size_t mo = (size_t)(c0 + k) * Mp + row;
-        ep.out[mo] = o[k];
-        reinterpret_cast<HT*>(ep.out_h)[mo] = h[k];
-        reinterpret_cast<HT*>(ep.out_l)[mo] = l[k];
+      for (int i = 0; i < 4; ++i) {
+        const int c = c0 + cl + i;
+        if (mma && c == r && r < ep.M) ov[i] += cj;
+        if (c >= r) store_out1<BF16>(ep, off + i, ov[i]);
       }
+      o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    }
+    *reinterpret_cast<float4*>(&tp[tp_idx(rr, cl)]) = o;
+  }
+  __syncwarp();
+  const int cs = lane >> 3, gr = lane & 7;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int cc = cs + 4 * j;
+    const float4 m = make_float4(tp[tp_idx(4 * gr, cc)], tp[tp_idx(4 * gr + 1, cc)],
+                                 tp[tp_idx(4 * gr + 2, cc)], tp[tp_idx(4 * gr + 3, cc)]);
+    const size_t mo = (size_t)(c0 + cc) * Mp + row0 + 4 * gr;
+    if (!diag_blk) {
+      store_out4<BF16>(ep, mo, m);
+    } else {
+      const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c0 + cc > row0 + 4 * gr + i) store_out1<BF16>(ep, mo + i, mv[i]);
     }
   }
+  __syncwarp();
 }
 
 // Everything one tile needs: its block coordinates, operand maps, the
@@ -701,8 +670,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                               jb == c.I, thf, f2th, thtb, pp, dpart, tp);
           }
         } else if constexpr (MODE == 2) {
-          gemm2_row<BF16>(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc,
-                          c.mma, c.ca, c.cb, c.cj, c.cz);
+#pragma unroll 1
+          for (int part = 0; part < 4; ++part) {
+            switch (part) {
+              case 0: acc_to_tp<0>(acc, tp, lane); break;
+              case 1: acc_to_tp<1>(acc, tp, lane); break;
+              case 2: acc_to_tp<2>(acc, tp, lane); break;
+              default: acc_to_tp<3>(acc, tp, lane); break;
+            }
+            gemm2_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
+                              jb == c.I, c.mma, c.ca, c.cb, c.cj, c.cz, tp);
+          }
         } else {
           refine_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc);
         }
