@@ -439,15 +439,22 @@ def main():
                 "achieved_tflops": 2 * alg / ((t1 + t2) * 1e-3) / 1e12,
                 "executed_tflops": 2 * 3 * tile_flops / ((t1 + t2) * 1e-3) / 1e12}
         if "mixed" in args.prec and l64 > 0:
-            o1, o2 = solver.time_kernels(M, N, prec=args.prec, reps=3)
+            o1, o2, o3 = solver.time_kernels(M, N, prec=args.prec, reps=3)
+            # each refinement step: slice GEMM, refinement product, stop-test
+            # product (the last step's stop test accepts D1 without a further
+            # slice GEMM)
             kern["oz_gemm_kernel"] = {
                 "what": "exact digit-slice D^2 of one refinement step", "ms": o1,
-                "launches_per_solve": l64 + 1, "ms_per_solve": o1 * (l64 + 1),
+                "launches_per_solve": l64, "ms_per_solve": o1 * l64,
                 "achieved_tflops": alg / (o1 * 1e-3) / 1e12,
                 "executed_tflops": (44 if M <= 16384 else 54) * tile_flops / (o1 * 1e-3) / 1e12}
             kern["tc_gemm_kernel<3>"] = {
                 "what": "refinement product (D^2 - D) D", "ms": o2, "launches_per_solve": l64,
                 "ms_per_solve": o2 * l64, "executed_tflops": 3 * tile_flops / (o2 * 1e-3) / 1e12}
+            kern["tc_gemm_kernel<4>"] = {
+                "what": "stop-test product W = D1^2 - D^2 (K = 3M)", "ms": o3,
+                "launches_per_solve": l64, "ms_per_solve": o3 * l64,
+                "executed_tflops": 9 * tile_flops / (o3 * 1e-3) / 1e12}
     except Exception as e:  # noqa: BLE001
         kern["error"] = str(e)
     roof = {"bound": "tensor", "achieved": None, "peak": bf16_peak, "unit": "TFLOP/s",
@@ -505,18 +512,22 @@ def main():
                          f"{t:.1f} s"}
 
     # kernel launches per solve: guess 4; each WHILE body holds two steps and
-    # runs (evaluations + 1) // 2 times, evaluations = applied steps + 1;
-    # split step 3 launches (GEMM1, control, GEMM2), FP64 step 3, slice
-    # refinement step 5 (slice, slice GEMM, finalize, control, product);
+    # runs (evaluations + 1) // 2 times, evaluations = applied steps + 1
+    # (slice refinement: = applied steps, the stop test of the last step
+    # ends the phase); split step 3 launches (GEMM1, control, GEMM2), FP64
+    # step 3, slice refinement step 8 (slice, slice GEMM, finalize, control,
+    # product, stop-test halves, stop-test product, stop-test control);
     # phase change 2; copy-out 1; energy 2
     split_phase = "mixed" in args.prec or args.prec in ("fp16x3", "bf16x3")
     f64_phase = "mixed" in args.prec or args.prec == "fp64"
-    ref_step = 5 if ("mixed" in args.prec and "oz_gemm_kernel" in kern) else 3
+    slices = "mixed" in args.prec and "oz_gemm_kernel" in kern
+    ref_step = 8 if slices else 3
     per_solve = 4 + 1 + 2
     if split_phase:
         per_solve += 6 * ((lp + 2) // 2)
     if f64_phase:
-        per_solve += 2 * ref_step * ((l64 + 2) // 2) + (2 if "mixed" in args.prec else 0)
+        evals = l64 if slices else l64 + 1
+        per_solve += 2 * ref_step * ((evals + 1) // 2) + (2 if "mixed" in args.prec else 0)
     launches = args.steps * per_solve
 
     if rank == 0:

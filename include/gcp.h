@@ -240,12 +240,12 @@ gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int h_dtype, v
  * step on the workspace left by the last gcp_solve on this handle (same M;
  * `prec` GCP_FP64 times the FP64 kernels, GCP_FP16X3/GCP_BF16X3 the
  * tensor-core ones and needs a prior split or mixed solve, GCP_MIXED_FP16
- * or GCP_MIXED_BF16 the two products of an exact-slice refinement step --
- * the digit-slice D^2 and the fp16 split (D^2 - D) D -- and needs a prior
- * mixed solve that used that refinement).  Each kernel is launched `reps`
- * times on opt->stream, bracketed by CUDA events; ms (host, 2 doubles)
- * receives the mean duration of the first and the second product in
- * milliseconds.  The workspace iterate is overwritten: solve again before
+ * or GCP_MIXED_BF16 the products of an exact-slice refinement step -- the
+ * digit-slice D^2, the fp16 split (D^2 - D) D and the stop-test product
+ * W = D1^2 - D^2 -- and needs a prior mixed solve that used that
+ * refinement).  Each kernel is launched `reps` times on opt->stream,
+ * bracketed by CUDA events; ms (host; 2 doubles, 3 for GCP_MIXED_*)
+ * receives the mean duration of each product in milliseconds.  The workspace iterate is overwritten: solve again before
  * reading results. */
 gcp_status gcp_time_kernels(void* handle, int M, int N, int prec, int reps, double* ms,
                             const gcp_options* opt);

@@ -80,6 +80,7 @@ struct Handle {
   OzOperands* oz_op = nullptr;
   TcOperands* oz_opD = nullptr;
   TcOperands* oz_opX = nullptr;
+  void* oz_emaps = nullptr;  // device maps of slices 0/1 as split halves (stop test)
 };
 
 void free_oz(Handle* h) {
@@ -99,6 +100,8 @@ void free_oz(Handle* h) {
   if (h->oz_op) oz_free_operands(h->oz_op);
   if (h->oz_opD) tc_free_operands(h->oz_opD);
   if (h->oz_opX) tc_free_operands(h->oz_opX);
+  cudaFree(h->oz_emaps);
+  h->oz_emaps = nullptr;
   h->oz_op = nullptr;
   h->oz_opD = h->oz_opX = nullptr;
   h->oz_mp = 0;
@@ -241,7 +244,8 @@ gcp_status ensure_oz(Handle* h, int Mp) {
   char err[256] = {0};
   if (oz_make_operands(&h->oz_op, h->oz_slices, Mp, err, sizeof err) ||
       tc_make_operands(&h->oz_opD, h->oz_dh, h->oz_dl, Mp, 0, err, sizeof err) ||
-      tc_make_operands(&h->oz_opX, h->oz_xh, h->oz_xl, Mp, 0, err, sizeof err))
+      tc_make_operands(&h->oz_opX, h->oz_xh, h->oz_xl, Mp, 0, err, sizeof err) ||
+      tc_make_device_maps(&h->oz_emaps, h->oz_slices[0], h->oz_slices[1], Mp, err, sizeof err))
     return fail(h, GCP_ERR_CUDA, "%s", err);
   h->oz_mp = Mp;
   return GCP_OK;
@@ -307,6 +311,20 @@ gcp_status rec_oz_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
                           h->oz_xscale, h->oz_rscale, M, Mp, h->st, s))
     return fail(h, GCP_ERR_CUDA, "McWeeny product launch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
+  if (ctl.stop == GCP_STOP_IDEMP_FRO) {
+    // stop test of the new iterate D1 from W = D1^2 - D^2 (one split
+    // product over [D | Delta | Delta] x [Delta | D | Delta]) instead of a
+    // second exact product; the operand buffers of the step are free now
+    launch_check_halves(h->D64[src], h->D64[src ^ 1], M, Mp, h->oz_dh, h->oz_dl, h->oz_xh,
+                        h->oz_xl, h->oz_slices[0], h->oz_slices[1], h->st, s);
+    if (tc_launch_check(h->oz_opD, h->oz_opX, h->oz_emaps, h->S64, h->D64[src ^ 1], h->part, M,
+                        Mp, h->st, s))
+      return fail(h, GCP_ERR_CUDA, "stop-test product launch failed: %s",
+                  cudaGetErrorString(cudaGetLastError()));
+    launch_check_control(h->part, tc_num_tiles(Mp), h->st,
+                         a.o.history_cap > 0 ? h->hist : nullptr, ctl, (unsigned long long)cond,
+                         use_cond, s);
+  }
   CK(cudaPeekAtLastError());
   return GCP_OK;
 }
@@ -1222,12 +1240,24 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   }
   CK(cudaEventRecord(e[3], s));
   CK(cudaEventSynchronize(e[3]));
-  float t1 = 0.f, t2 = 0.f;
+  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
   CK(cudaEventElapsedTime(&t1, e[0], e[1]));
   CK(cudaEventElapsedTime(&t2, e[2], e[3]));
+  if (refine) {
+    // the stop-test product of the step (reuses the first two events)
+    CK(cudaEventRecord(e[0], s));
+    for (int r = 0; r < reps; ++r)
+      if (tc_launch_check(h->oz_opD, h->oz_opX, h->oz_emaps, h->S64, h->D64[1], h->part, M,
+                          h->oz_mp, h->st, s))
+        return fail(h, GCP_ERR_CUDA, "stop-test product launch failed");
+    CK(cudaEventRecord(e[1], s));
+    CK(cudaEventSynchronize(e[1]));
+    CK(cudaEventElapsedTime(&t3, e[0], e[1]));
+  }
   for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
   ms[0] = t1 / reps;
   ms[1] = t2 / reps;
+  if (refine) ms[2] = t3 / reps;
   State hs;
   CK(cudaMemcpy(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost));
   if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");

@@ -283,6 +283,53 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
   if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
+// Stop test after a refinement step D -> D1, from the check product's
+// per-tile partials (Tr D1, Tr D1^2, -, R1^2): the iterate the next step
+// would evaluate exactly is accepted now when R1 = ||D1^2 - D1||_F <= tol.
+// Otherwise nothing changes and the next step evaluates D1 with the exact
+// product (and stops there if the two disagree about tol).  The WHILE
+// condition is set after this kernel as after the step's control kernel.
+__global__ void __launch_bounds__(kCtlThreads) check_control_kernel(
+    const double* __restrict__ part, int ntiles, State* st, double* hist, Ctl ctl,
+    cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double red[32 * 5];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (!st->stopped)
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+      const double* p = part + (size_t)t * kPartFields;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += p[k];
+    }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  if (!st->stopped && !st->timeout) {
+    const double T1 = v[0], T2 = v[1], R = sqrt(fmax(v[3], 0.0));
+    if (isfinite(T1) && isfinite(T2) && isfinite(R) && R <= ctl.tol) {
+      st->T1 = T1;
+      st->T2 = T2;
+      st->T3 = __longlong_as_double(0x7ff8000000000000ll);  // not evaluated
+      st->R = R;
+      st->stopped = 1;
+      st->apply = 0;
+      st->converged = 1;
+      st->status = GCP_OK;
+      if (hist && st->hist_n < ctl.hist_cap) {
+        double* rec = hist + (size_t)st->hist_n * GCP_HISTORY_FIELDS;
+        rec[0] = st->n;
+        rec[1] = T1;
+        rec[2] = T2;
+        rec[3] = st->T3;
+        rec[4] = R;
+        rec[5] = st->T3;
+        rec[6] = st->E;
+        rec[7] = ctl.phase;
+        st->hist_n += 1;
+      }
+    }
+  }
+  if (use_cond) cudaGraphSetConditional(cond, st->stopped ? 0u : 1u);
+}
+
 // Batched control: block b decides for instance b from its own tiles'
 // partial sums (per-instance c_n and stop mask).
 __global__ void __launch_bounds__(kCtlThreads) batch_control_kernel(const double* __restrict__ part,
@@ -460,6 +507,13 @@ void launch_control(const double* part, int ntiles, State* st, double* hist, Ctl
                     unsigned long long cond_handle, int use_cond, cudaStream_t s) {
   control_kernel<<<1, kCtlThreads, 0, s>>>(part, ntiles, st, hist, ctl,
                                            (cudaGraphConditionalHandle)cond_handle, use_cond);
+}
+
+void launch_check_control(const double* part, int ntiles, State* st, double* hist, Ctl ctl,
+                          unsigned long long cond_handle, int use_cond, cudaStream_t s) {
+  check_control_kernel<<<1, kCtlThreads, 0, s>>>(part, ntiles, st, hist, ctl,
+                                                 (cudaGraphConditionalHandle)cond_handle,
+                                                 use_cond);
 }
 
 void launch_state_init(State* st, int phase, cudaStream_t s) {

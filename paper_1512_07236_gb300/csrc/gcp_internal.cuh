@@ -58,6 +58,15 @@ constexpr int kPartFields = 6;  // T1, T2, T3, R^2, E, spare
 // operand halves (gcp_ozaki.cu).
 constexpr int kOzSlices = 9;
 constexpr double kRefScale = 16384.0;  // 2^14
+// Scale of Delta = D1 - D in the stop-test product after a refinement step:
+// 2^(13 - e) with 2^e > 2 R, R = ||D^2 - D||_F of the iterate before the
+// step; D1 - D = X((1 - a) I - 2D), |a| <= 0.1, so |Delta_ij| <= 1.2 R and
+// the scaled entries stay below 2^13.
+__host__ __device__ inline double check_delta_scale(double R) {
+  int e = 0;
+  frexp(2.0 * R, &e);  // 2 R < 2^e
+  return ldexp(1.0, 13 - e);
+}
 
 // Per-instance descriptor of a batched solve (device memory).  Every
 // instance has its own state, buffers and slices of the batched work lists.
@@ -123,6 +132,10 @@ void launch_f64_gemm2(const double* S, const double* D, double* Dn, int M, int l
 // ---- control (gcp_control.cu) --------------------------------------------
 void launch_control(const double* part, int ntiles, State* st, double* hist, Ctl ctl,
                     unsigned long long cond_handle, int use_cond, cudaStream_t s);
+// Stop test after a refinement step from the check product's partials
+// (Tr D1, Tr D1^2, -, R1^2): stops the phase, converged, when R1 <= tol.
+void launch_check_control(const double* part, int ntiles, State* st, double* hist, Ctl ctl,
+                          unsigned long long cond_handle, int use_cond, cudaStream_t s);
 void launch_state_init(State* st, int phase, cudaStream_t s);
 void launch_phase_begin(State* st, int phase, cudaStream_t s);
 // D_out = buf[parity] converted to the output dtype (FP64 source).
@@ -174,6 +187,17 @@ void tc_set_smem_attrs();
 int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const double* S64,
                         const double* D64, double* Dn64, const double* xscale,
                         const double* dscale, int M, int Mp, State* st, cudaStream_t s);
+// W = D1^2 - D^2 from the halves of D (opD, scale kRefScale), of
+// Delta = D1 - D (opDelta, scale check_delta_scale(R)) and of Delta at the
+// scale kRefScale (emaps, device maps), and the per-tile partials of
+// D1^2 - D1 = S + W - D1.
+int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void* emaps,
+                    const double* S64, const double* D1, double* part, int M, int Mp, State* st,
+                    cudaStream_t s);
+// Device copies (cudaMalloc'ed, freed with cudaFree) of the hi/lo tensor
+// maps of a pair of Mp x Mp fp16 arrays, for operands named through memory.
+int tc_make_device_maps(void** dev, const void* hi, const void* lo, int Mp, char* err,
+                        int errlen);
 
 // ---- exact slice products (gcp_ozaki.cu) ---------------------------------
 // D (FP64, M x M) -> per-row scale 2^e_i with |D_ij| <= 2^e_i / 2, nine
@@ -191,6 +215,11 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
 // kernel, and the fp16 halves of xscale_i X_ij, X = S - D, with a power of
 // two xscale_i per row (max_j |xscale_i X_ij| < 2^13).
 int oz_finalize_blocks(int M);
+// fp16 halves (Mp x Mp, zero padded) of kRefScale D, of s Delta with
+// s = check_delta_scale(State::R) and of kRefScale Delta, Delta = D1 - D.
+void launch_check_halves(const double* D64, const double* D1, int M, int Mp, void* Dh, void* Dl,
+                         void* Xh, void* Xl, void* Eh, void* El, const State* st,
+                         cudaStream_t s);
 void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s);
 // Digit bits b and slice count of the slicing for an M-long inner dimension.

@@ -272,6 +272,40 @@ __device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
   }
 }
 
+// ---- operands of the stop-test product after a refinement step ----------------
+// fp16 halves of kRefScale D, of s Delta (Delta = D1 - D, |Delta| <= 1.2 R,
+// s = check_delta_scale(R) puts it near 2^12, clear of the fp16 subnormals)
+// and of kRefScale Delta: D Delta, Delta D and Delta (kRefScale Delta) then
+// share the scale kRefScale s and one accumulator.  The last operand loses
+// Delta's smallest entries to subnormals, an error of second order.
+__global__ void __launch_bounds__(256) check_halves_kernel(
+    const double* __restrict__ D, const double* __restrict__ D1, int M, int Mp,
+    __half* __restrict__ Dh, __half* __restrict__ Dl, __half* __restrict__ Xh,
+    __half* __restrict__ Xl, __half* __restrict__ Eh, __half* __restrict__ El,
+    const State* __restrict__ st) {
+  if (st->stopped) return;
+  const float sd = (float)check_delta_scale(st->R);  // a power of two
+  const size_t n = (size_t)Mp * Mp;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
+       o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o / Mp), j = (int)(o % Mp);
+    double d = 0.0, dd = 0.0;
+    if (i < M && j < M) {
+      d = D[(size_t)i * M + j];
+      dd = D1[(size_t)i * M + j] - d;
+    }
+    const float df = (float)dd;
+    const float y = (float)d * (float)kRefScale, z = df * sd, w = df * (float)kRefScale;
+    const __half yh = __float2half_rn(y), zh = __float2half_rn(z), wh = __float2half_rn(w);
+    Dh[o] = yh;
+    Dl[o] = __float2half_rn(y - __half2float(yh));
+    Xh[o] = zh;
+    Xl[o] = __float2half_rn(z - __half2float(zh));
+    Eh[o] = wh;
+    El[o] = __float2half_rn(w - __half2float(wh));
+  }
+}
+
 __global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
     const double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
     double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
@@ -679,6 +713,15 @@ int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int err
 }
 
 int oz_finalize_blocks(int M) { return M < 1024 ? M : 1024; }
+
+void launch_check_halves(const double* D64, const double* D1, int M, int Mp, void* Dh, void* Dl,
+                         void* Xh, void* Xl, void* Eh, void* El, const State* st,
+                         cudaStream_t s) {
+  const size_t n = (size_t)Mp * Mp;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  check_halves_kernel<<<grid, 256, 0, s>>>(D64, D1, M, Mp, (__half*)Dh, (__half*)Dl, (__half*)Xh,
+                                           (__half*)Xl, (__half*)Eh, (__half*)El, st);
+}
 
 void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s) {

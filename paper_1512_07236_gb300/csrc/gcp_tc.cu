@@ -86,7 +86,7 @@ constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per d
 // product keeps that shared memory as L1 cache for its row-wise FP64 loads.
 template <int MODE>
 __host__ __device__ constexpr uint32_t smem_bytes() {
-  return STAGES * kStageBytes + (MODE != 3 ? kTpBytes : 0u) + 1024;
+  return STAGES * kStageBytes + (MODE == 1 || MODE == 2 ? kTpBytes : 0u) + 1024;
 }
 static_assert(smem_bytes<1>() + 768 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
@@ -112,6 +112,10 @@ struct Epi {
   const double* rs_x;  // row scales of the X operand
   const double* rs_d;  // 2^e_j: row j of the D operand holds kRefScale D_jk / 2^e_j
   int ld64;
+  // mode 4 (stop test after a refinement step): S64 = D^2 (exact), D64 = the
+  // new iterate D1, the product W = D1^2 - D^2 in the scale kRefScale s_Delta;
+  // emaps: device maps of Delta at the scale kRefScale (B of the Delta^2 part)
+  const CUtensorMap* emaps;
 };
 
 // Linear tile index -> (I, J): I a 128-row block, J a 256-column block,
@@ -160,6 +164,32 @@ __device__ __forceinline__ void refine_row(const Epi& ep, int row, int c_base, b
     const double v = sv - 2.0 * (wr * ep.rs_d[c]) * (double)acc[k] - g * (sv - ep.D64[o]);
     ep.Dn64[o] = v;
     if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
+  }
+}
+
+// Stop-test epilogue of one thread after a refinement step D -> D1 (mode 4):
+// acc[] = kRefScale s_Delta W_row,c with W = D1^2 - D^2 = D Delta + Delta D +
+// Delta^2, Delta = D1 - D; with S = D^2 exact, D1^2 - D1 = S + W - D1 is
+// formed in FP64 (S and D1 are O(1), the result is ~R1).  Sums: the
+// residual R1^2 (FP32 per lane, weight 2 above the diagonal), Tr D1 and
+// Tr D1^2 = Tr S + Tr W (FP64, diagonal only).
+__device__ __forceinline__ void check_row(const Epi& ep, int row, int c_base, bool diag_blk,
+                                          const float (&acc)[128], float inv_scale,
+                                          float (&pp)[3], double (&dpart)[5]) {
+  if (row >= ep.M) return;
+#pragma unroll 4
+  for (int k = 0; k < 128; ++k) {
+    const int c = c_base + k;
+    if (c >= ep.M || (diag_blk && c < row)) continue;
+    const size_t o = (size_t)row * ep.ld64 + c;
+    const double sw = ep.S64[o] + (double)(acc[k] * inv_scale);  // D1^2, exact scaling
+    const double d1 = ep.D64[o];
+    const float x1 = (float)(sw - d1);
+    pp[1] = fmaf((c == row ? 1.f : 2.f) * x1, x1, pp[1]);
+    if (c == row) {
+      dpart[0] += d1;
+      dpart[1] += sw;
+    }
   }
 }
 
@@ -467,7 +497,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
   }
   const State* st = c.ep.st;
   c.mma = !c.skip && (MODE == 1 || st->apply != 0);
-  c.nkb = c.mma ? c.ep.Mp / BK : 0;
+  c.nkb = c.mma ? (MODE == 4 ? 3 : 1) * (c.ep.Mp / BK) : 0;
   c.ca = c.cb = c.cj = c.cz = 0.f;
   if (MODE == 2 && !c.skip) {
     const double th = st->theta, g3 = st->g3;
@@ -542,13 +572,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const uint32_t stage = sbase + s * kStageBytes;
           mbar_expect_tx(&full_bar[s], kStageBytes);
-          const int kx = kb * BK;
-          tma_load_2d(c.ah, &full_bar[s], stage, kx, c.I * BM);
-          tma_load_2d(c.al, &full_bar[s], stage + kABytes, kx, c.I * BM);
-          tma_load_2d(c.bh, &full_bar[s], stage + 2 * kABytes, kx, c.J * BN);
-          tma_load_2d(c.bh, &full_bar[s], stage + 2 * kABytes + kBBytes / 2, kx, c.J * BN + 128);
-          tma_load_2d(c.bl, &full_bar[s], stage + 2 * kABytes + kBBytes, kx, c.J * BN);
-          tma_load_2d(c.bl, &full_bar[s], stage + 2 * kABytes + kBBytes + kBBytes / 2, kx,
+          int kx = kb * BK;
+          const CUtensorMap *ah = c.ah, *al = c.al, *bh = c.bh, *bl = c.bl;
+          if (MODE == 4) {
+            // K = [0, 3 Mp): A rows [D | Delta | Delta], B rows [Delta | D | Delta]
+            // (maps: a* = D, b* = Delta, emaps = Delta at D's scale), so the
+            // sum is D Delta + Delta D + Delta^2, all in the scale kRefScale s_Delta
+            const int kseg = c.ep.Mp / BK, seg = kb / kseg;
+            kx = (kb - seg * kseg) * BK;
+            if (seg >= 1) {
+              ah = c.bh;
+              al = c.bl;
+            }
+            if (seg == 1) {
+              bh = c.ah;
+              bl = c.al;
+            } else if (seg == 2) {
+              bh = &c.ep.emaps[0];
+              bl = &c.ep.emaps[1];
+            }
+          }
+          tma_load_2d(ah, &full_bar[s], stage, kx, c.I * BM);
+          tma_load_2d(al, &full_bar[s], stage + kABytes, kx, c.I * BM);
+          tma_load_2d(bh, &full_bar[s], stage + 2 * kABytes, kx, c.J * BN);
+          tma_load_2d(bh, &full_bar[s], stage + 2 * kABytes + kBBytes / 2, kx, c.J * BN + 128);
+          tma_load_2d(bl, &full_bar[s], stage + 2 * kABytes + kBBytes, kx, c.J * BN);
+          tma_load_2d(bl, &full_bar[s], stage + 2 * kABytes + kBBytes + kBBytes / 2, kx,
                       c.J * BN + 128);
         }
       }
@@ -681,11 +730,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             gemm2_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
                               jb == c.I, c.mma, c.ca, c.cb, c.cj, c.cz, tp);
           }
+        } else if constexpr (MODE == 4) {
+          const float inv = (float)(1.0 / (kRefScale * check_delta_scale(c.ep.st->R)));
+          check_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc, inv,
+                    pp, dpart);
         } else {
           refine_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc);
         }
       }
-      if (MODE == 1) {
+      if (MODE == 1 || MODE == 4) {
         // FP64 arithmetic is slow on this part: only warps on a diagonal
         // block (warp-uniform) reduce the FP64 sums, and six lanes of warp
         // 0 add the warps' rows of the table in parallel.  The table is
@@ -904,6 +957,37 @@ int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const doub
   ep.rs_d = dscale;
   ep.ld64 = M;
   return launch_tc<3, false, false>(opX, opD, ep, nullptr, nullptr, s);
+}
+
+int tc_make_device_maps(void** dev, const void* hi, const void* lo, int Mp, char* err,
+                        int errlen) {
+  CUtensorMap m[2];
+  if (encode_map(&m[0], hi, Mp, 0, err, errlen) || encode_map(&m[1], lo, Mp, 0, err, errlen))
+    return 1;
+  if (cudaMalloc(dev, sizeof m) != cudaSuccess ||
+      cudaMemcpy(*dev, m, sizeof m, cudaMemcpyHostToDevice) != cudaSuccess) {
+    snprintf(err, errlen, "device tensor maps: %s", cudaGetErrorString(cudaGetLastError()));
+    return 1;
+  }
+  return 0;
+}
+
+int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void* emaps,
+                    const double* S64, const double* D1, double* part, int M, int Mp, State* st,
+                    cudaStream_t s) {
+  Epi ep{};
+  ep.emaps = (const CUtensorMap*)emaps;
+  ep.st = st;
+  ep.M = M;
+  ep.Mp = Mp;
+  ep.ntiles = tc_num_tiles(Mp);
+  ep.split_scale = 1.0f;
+  ep.inv_s2 = 1.0f;
+  ep.part = part;
+  ep.S64 = S64;
+  ep.D64 = D1;
+  ep.ld64 = M;
+  return launch_tc<4, false, false>(opD, opDelta, ep, nullptr, nullptr, s);
 }
 
 size_t tc_map_bytes() { return 6 * sizeof(CUtensorMap); }

@@ -273,13 +273,16 @@ class Solver:
         """Mean duration (ms) of the two products of one step, CUDA events on
         the current stream; needs a prior solve of size M on this handle.
         prec "fp16x3"/"bf16x3": GEMM1 and GEMM2 of a split step; "fp64": the
-        FP64 products; "mixed_fp16"/"mixed_bf16": the digit-slice D^2 and the
-        (D^2 - D) D product of an exact-slice refinement step."""
-        ms = (C.c_double * 2)()
+        FP64 products; "mixed_fp16"/"mixed_bf16": the digit-slice D^2, the
+        (D^2 - D) D product and the stop-test product of an exact-slice
+        refinement step (three values)."""
+        ms = (C.c_double * 3)()
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         o = make_options()
         self._check(self.lib.gcp_time_kernels(self.h, int(M), int(N), p, int(reps), ms,
                                               C.byref(o)))
+        if p in (PRECISIONS["mixed_fp16"], PRECISIONS["mixed_bf16"]):
+            return ms[0], ms[1], ms[2]
         return ms[0], ms[1]
 
     def history(self, cap=1000):
