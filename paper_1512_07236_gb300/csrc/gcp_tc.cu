@@ -1,5 +1,8 @@
 // Split-precision tensor-core products of one GCP step (sm_103a: tcgen05 +
-// TMEM + TMA), with the step's elementwise work fused into the epilogues.
+// TMEM + TMA), with the step's elementwise work fused into the epilogues:
+// mode 1 GEMM1, mode 2 GEMM2 of the split phase; mode 3 the product of an
+// exact-slice refinement step, mode 4 the stop-test product after it
+// (W = D1^2 - D^2 over a K = 3M concatenation of operands).
 //
 // State.  The iterate is held shifted, X = D - theta J (J = identity on the
 // unpadded M x M block), in FP32, plus two 16-bit halves of s X (s = 2^14):
@@ -19,8 +22,10 @@
 // ever holds one K chunk of 128 (24 MMAs; 32 in the refinement product):
 // eight drain warps move each chunk from TMEM into FP32 registers with
 // round-to-nearest adds while the MMA warp fills the other of two TMEM
-// buffers.  (Chunks of 64 cost 16% more
-// time in GEMM1 at M = 8192 for no measurable gain in accuracy.)
+// buffers.  (Chunks of 64 cost 16% more time in GEMM1 at M = 8192 for no
+// measurable gain in accuracy; longer first chunks of a tile, which would
+// keep the MMAs going through more of the previous tile's epilogue, moved
+// the subspace error past 1e-6 at M = 8192.)
 //
 // GEMM1 (Y = X X).  With S = D^2 = theta^2 J + Sigma, Sigma = 2 theta X + Y,
 // the epilogue writes Sigma (FP32 + halves, exactly symmetric) and per-tile
@@ -43,9 +48,9 @@
 // and columns 128((w-4)/4)..).  The first warpgroup hands registers to the
 // other two (setmaxnreg: 40 and 232 a thread against 168 at launch), which
 // hold the 128 x 256 FP32 accumulator, 128 values a thread, without
-// spilling.  Blocks below the diagonal
-// inside a tile are skipped in the epilogue; every element above the
-// diagonal is stored twice (direct and mirrored).  Every wait is bounded
+// spilling.  Blocks below the diagonal inside a tile are skipped in the
+// epilogue; every element above the diagonal is stored twice (direct and
+// mirrored).  Every wait is bounded
 // (2 s); on expiry the kernel records State::timeout and winds down, still
 // freeing its TMEM.
 #include <cuda.h>
@@ -99,7 +104,7 @@ struct Epi {
   void* out_l;
   const void* H;     // optional, for sum D o H (mode 1)
   int h_f64, ldh;
-  double* part;      // per-tile partials (mode 1)
+  double* part;      // per-tile partials (modes 1 and 4)
   State* st;
   int M, Mp, ntiles;
   float split_scale;  // s
