@@ -182,7 +182,8 @@ __device__ __forceinline__ void check_row(const Epi& ep, int row, int c_base, bo
                                           const float (&acc)[128], float inv_scale,
                                           float (&pp)[3], double (&dpart)[5]) {
   if (row >= ep.M) return;
-#pragma unroll 4
+  // fully unrolled: acc[] stays in registers
+#pragma unroll
   for (int k = 0; k < 128; ++k) {
     const int c = c_base + k;
     if (c >= ep.M || (diag_blk && c < row)) continue;
