@@ -144,7 +144,10 @@ typedef struct {
   int iters_fp64;    /* steps applied in FP64 */
   double trace;      /* Tr D of the returned D (FP64 sum) */
   double energy;     /* E = Tr(H D) of the returned D */
-  double idem_fro;   /* ||D^2 - D||_F at the last evaluated iterate */
+  double idem_fro;   /* ||D^2 - D||_F at the last evaluated iterate (after an
+                        exact-slice refinement step accepted by the stop-test
+                        product: ||S + W - D1||_F, S = D^2 exact, W = D1^2 - D^2
+                        from a split product; ~1e-7 of the step's residual) */
   double trace_ddbar;/* Tr(D - D^2) at the last evaluated iterate */
   double c_last;     /* last c_n used */
   double mu, beta2, hmin, hmax; /* guess parameters (Eq. pmcpguess); beta2 is
