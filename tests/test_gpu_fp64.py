@@ -160,3 +160,18 @@ def test_bad_arguments_rejected(solver):
         solver.solve(H, 9, prec="fp64")
     with pytest.raises(gcp.GCPError):
         solver.solve(H, 2, prec=17)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp16"])
+def test_nonfinite_hamiltonian_is_a_status(solver, prec):
+    """A NaN in H makes the first evaluation's traces non-finite: the control
+    kernel stops with GCP_ERR_NONFINITE and the handle stays usable."""
+    from paper_1512_07236_gb300 import gcp
+    H, _, _ = inputs.rotated_spectrum(64, 16, seed=12)
+    Hn = H.copy()
+    Hn[3, 5] = Hn[5, 3] = np.nan
+    with pytest.raises(gcp.GCPError) as err:
+        solver.solve(_dev(Hn), 16, prec=prec)
+    assert err.value.status == gcp.ERR_NONFINITE
+    D, info = solver.solve(_dev(H), 16, prec="fp64")
+    assert info["status"] == 0
