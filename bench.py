@@ -179,6 +179,14 @@ def oracle_sample(H, N, iters):
     return time.perf_counter() - t0, r["iters"]
 
 
+# The headline metric, shared by both arms.
+METRIC = "GCP effective TFLOP/s (dense-equivalent 4 M^3 per step) to ||D^2-D||_F<=1e-6"
+
+
+def workload_name(M, N, gap):
+    return f"dense rotated spectrum M={M} N={N} gap={gap}, tol {TOL}"
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
@@ -195,12 +203,12 @@ def run_reference(args, rank, world):
     per_step = statistics.mean(times)
     value = flops_step / per_step / 1e12
     line = {
-        "impl": "reference", "metric": "GCP effective TFLOP/s (FP64 CPU oracle)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"dense rotated spectrum M={M} N={N} gap={args.gap}",
-                   "M": M, "N": N, "gap": args.gap,
+        "config": {"workload": workload_name(M, N, args.gap),
+                   "M": M, "N": N, "gap": args.gap, "prec": "fp64 (CPU oracle)",
                    "sample": f"{args.cpu_iters} purification steps per timed step"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_cores(),
                          "kind": "oracle",
@@ -532,13 +540,12 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "GCP effective TFLOP/s (dense-equivalent 4 M^3 per step) to ||D^2-D||_F<=1e-6",
+            "metric": METRIC,
             "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16x3+f64",
             "data": "synthetic",
-            "config": {"workload": f"dense rotated spectrum M={M} N={N} gap={args.gap}, "
-                                   f"{args.prec}, tol {TOL}",
+            "config": {"workload": workload_name(M, N, args.gap),
                        "M": M, "N": N, "gap": args.gap, "prec": args.prec,
                        "guess": args.guess, "method": args.method,
                        "iters": iters, "iters_lowp": lp, "iters_fp64": l64,
