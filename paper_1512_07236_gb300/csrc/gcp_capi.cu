@@ -45,6 +45,8 @@ struct Handle {
   void* Sl = nullptr;
   TcOperands* opX[2] = {nullptr, nullptr};
   TcOperands* opS = nullptr;
+  // scratch of the tensor-core kernels (tile hand-over, two slots per CTA)
+  float* tcs = nullptr;
   // scalars and partials
   double* part = nullptr;
   size_t part_n = 0;
@@ -185,7 +187,16 @@ gcp_status ensure_f64(Handle* h, int M) {
   return GCP_OK;
 }
 
+gcp_status ensure_tcs(Handle* h) {
+  if (h->tcs) return GCP_OK;
+  drop_graph(h);
+  CK(cudaMalloc((void**)&h->tcs, tc_scratch_bytes()));
+  return GCP_OK;
+}
+
 gcp_status ensure_split(Handle* h, int Mp, int bf16) {
+  gcp_status r = ensure_tcs(h);
+  if (r != GCP_OK) return r;
   if (Mp == h->mp && bf16 == h->tc_bf16) return GCP_OK;
   drop_graph(h);
   for (int i = 0; i < 2; ++i) {
@@ -230,6 +241,8 @@ gcp_status ensure_split(Handle* h, int Mp, int bf16) {
 }
 
 gcp_status ensure_oz(Handle* h, int Mp) {
+  gcp_status r = ensure_tcs(h);
+  if (r != GCP_OK) return r;
   if (Mp == h->oz_mp) return GCP_OK;
   drop_graph(h);
   free_oz(h);
@@ -308,7 +321,7 @@ gcp_status rec_oz_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
   launch_control(h->part, oz_finalize_blocks(M), h->st, a.o.history_cap > 0 ? h->hist : nullptr,
                  ctl, (unsigned long long)cond, use_cond, s);
   if (tc_launch_mcweeny64(h->oz_opX, h->oz_opD, h->S64, h->D64[src], h->D64[src ^ 1],
-                          h->oz_xscale, h->oz_rscale, M, Mp, h->st, s))
+                          h->oz_xscale, h->oz_rscale, M, Mp, h->st, h->tcs, s))
     return fail(h, GCP_ERR_CUDA, "McWeeny product launch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   if (ctl.stop == GCP_STOP_IDEMP_FRO) {
@@ -318,7 +331,7 @@ gcp_status rec_oz_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
     launch_check_halves(h->D64[src], h->D64[src ^ 1], M, Mp, h->oz_dh, h->oz_dl, h->oz_xh,
                         h->oz_xl, h->oz_slices[0], h->oz_slices[1], h->st, s);
     if (tc_launch_check(h->oz_opD, h->oz_opX, h->oz_emaps, h->S64, h->D64[src ^ 1], h->part, M,
-                        Mp, h->st, s))
+                        Mp, h->st, h->tcs, s))
       return fail(h, GCP_ERR_CUDA, "stop-test product launch failed: %s",
                   cudaGetErrorString(cudaGetLastError()));
     launch_check_control(h->part, tc_num_tiles(Mp), h->st,
@@ -339,13 +352,13 @@ gcp_status rec_split_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
   const int M = a.M, Mp = h->mp, bf = h->tc_bf16;
   const void* Hh = a.o.history_cap > 0 ? a.H : nullptr;
   if (tc_launch_gemm1(h->opX[src], h->X[src], h->Sig, h->Sh, h->Sl, M, Mp, Hh, a.h_f64, a.ld,
-                      h->part, h->st, bf, kSplitScale, nullptr, s))
+                      h->part, h->st, bf, kSplitScale, h->tcs, s))
     return fail(h, GCP_ERR_CUDA, "tcgen05 GEMM1 launch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   launch_control(h->part, tc_num_tiles(Mp), h->st, a.o.history_cap > 0 ? h->hist : nullptr, ctl,
                  (unsigned long long)cond, use_cond, s);
   if (tc_launch_gemm2(h->opS, h->opX[src], h->X[src], h->Sig, h->X[src ^ 1], h->Xh[src ^ 1],
-                      h->Xl[src ^ 1], M, Mp, h->st, bf, kSplitScale, nullptr, s))
+                      h->Xl[src ^ 1], M, Mp, h->st, bf, kSplitScale, h->tcs, s))
     return fail(h, GCP_ERR_CUDA, "tcgen05 GEMM2 launch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   CK(cudaPeekAtLastError());
@@ -535,6 +548,7 @@ gcp_status gcp_destroy(void* hv) {
   if (h->bexec) cudaGraphExecDestroy(h->bexec);
   if (h->bgraph) cudaGraphDestroy(h->bgraph);
   cudaFree(h->arena);
+  cudaFree(h->tcs);
   adjoint_free(h->adj);
   free_oz(h);
   for (int i = 0; i < 2; ++i) {
@@ -811,6 +825,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   }
   const int nb = (int)idx.size();
   if (nb == 0) return GCP_OK;
+  if (split && (r = ensure_tcs(h)) != GCP_OK) return r;
 
   // ---- layout of the arena -------------------------------------------
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1005,10 +1020,10 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   c1.method = c0.method = o.method;
 
   auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
-    if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, ss))
+    if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched GEMM1 launch failed");
     launch_batch_control(part, items_d, nb, c1, ss);
-    if (tc_launch_batch_gemm(2, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, ss))
+    if (tc_launch_batch_gemm(2, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched GEMM2 launch failed");
     launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
     CK(cudaPeekAtLastError());
@@ -1029,7 +1044,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       return fail(h, GCP_ERR_CUDA, "batched slice GEMM launch failed");
     launch_batch_oz_finalize(items_d, nb, maxM, part, ss);
     launch_batch_control(part, items_d, nb, c0, ss);
-    if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, ss))
+    if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched refinement product launch failed");
     launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
     CK(cudaPeekAtLastError());
@@ -1217,7 +1232,7 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
         return fail(h, GCP_ERR_CUDA, "slice GEMM launch failed");
     } else if (split) {
       if (tc_launch_gemm1(h->opX[0], h->X[0], h->Sig, h->Sh, h->Sl, M, Mp, nullptr, 1, M, h->part,
-                          h->st, bf, kSplitScale, nullptr, s))
+                          h->st, bf, kSplitScale, h->tcs, s))
         return fail(h, GCP_ERR_CUDA, "GEMM1 launch failed");
     } else {
       launch_f64_gemm1(h->D64[0], h->S64, M, M, nullptr, 1, M, h->part, h->st, s);
@@ -1228,11 +1243,11 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   for (int r = 0; r < reps; ++r) {
     if (refine) {
       if (tc_launch_mcweeny64(h->oz_opX, h->oz_opD, h->S64, h->D64[0], h->D64[1], h->oz_xscale,
-                              h->oz_rscale, M, h->oz_mp, h->st, s))
+                              h->oz_rscale, M, h->oz_mp, h->st, h->tcs, s))
         return fail(h, GCP_ERR_CUDA, "refinement product launch failed");
     } else if (split) {
       if (tc_launch_gemm2(h->opS, h->opX[0], h->X[0], h->Sig, h->X[1], h->Xh[1], h->Xl[1], M, Mp,
-                          h->st, bf, kSplitScale, nullptr, s))
+                          h->st, bf, kSplitScale, h->tcs, s))
         return fail(h, GCP_ERR_CUDA, "GEMM2 launch failed");
     } else {
       launch_f64_gemm2(h->S64, h->D64[0], h->D64[1], M, M, h->st, s);
@@ -1248,7 +1263,7 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
     CK(cudaEventRecord(e[0], s));
     for (int r = 0; r < reps; ++r)
       if (tc_launch_check(h->oz_opD, h->oz_opX, h->oz_emaps, h->S64, h->D64[1], h->part, M,
-                          h->oz_mp, h->st, s))
+                          h->oz_mp, h->st, h->tcs, s))
         return fail(h, GCP_ERR_CUDA, "stop-test product launch failed");
     CK(cudaEventRecord(e[1], s));
     CK(cudaEventSynchronize(e[1]));

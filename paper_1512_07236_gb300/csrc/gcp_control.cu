@@ -483,7 +483,8 @@ __global__ void d_to_x_kernel(const I* __restrict__ D, int M, int ld, float* __r
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Mp; j += gridDim.x * blockDim.x) {
     double v = 0.0;
     if (i < M && j < M) {
-      v = (double)D[(size_t)i * ld + j];
+      // the upper triangle of D only (exactly symmetric split state)
+      v = (double)(i <= j ? D[(size_t)i * ld + j] : D[(size_t)j * ld + i]);
       if (i == j) v -= theta;
     }
     const float x = (float)v;

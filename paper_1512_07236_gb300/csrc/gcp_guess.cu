@@ -205,7 +205,10 @@ __global__ void guess_write_x_kernel(const T* __restrict__ H, int M, int ld, flo
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Mp; j += gridDim.x * blockDim.x) {
     double v = 0.0;
     if (i < M && j < M) {
-      v = -beta2 * (double)H[(size_t)i * ld + j];
+      // the upper triangle of H only: the split state is exactly symmetric
+      // (the tensor-core epilogues write each mirrored element from the
+      // same inputs as the direct one)
+      v = -beta2 * (double)(i <= j ? H[(size_t)i * ld + j] : H[(size_t)j * ld + i]);
       if (i == j) v += beta2 * mu;
     }
     const float x = (float)v;
@@ -356,7 +359,8 @@ __global__ void batch_guess_write_x_kernel(const BatchItem* items, float scale) 
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.Mp; j += gridDim.x * blockDim.x) {
     double v = 0.0;
     if (i < it.M && j < it.M) {
-      v = -beta2 * (double)H[(size_t)i * it.ld + j];
+      // the upper triangle of H only (exactly symmetric split state)
+      v = -beta2 * (double)(i <= j ? H[(size_t)i * it.ld + j] : H[(size_t)j * it.ld + i]);
       if (i == j) v += beta2 * mu;
     }
     const float x = (float)v;

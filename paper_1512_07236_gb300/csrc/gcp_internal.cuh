@@ -173,12 +173,20 @@ int tc_make_operands(TcOperands** op, const void* hi, const void* lo, int Mp, in
 void tc_free_operands(TcOperands* op);
 // Mode 1: Y = X X, Sigma = 2 theta X + Y, partials.  Mode 2: Z = X Sigma,
 // X+ update.  See gcp_tc.cu for the epilogue formulas.
+// Every tensor-core launch takes `scratch`, tc_scratch_bytes() of device
+// memory: the drain warps hand each finished tile to the epilogue warps
+// through two 128 x 256 FP32 slots per CTA.
+size_t tc_scratch_bytes();
+// wait_ns: bound of every device-side wait (0: the default 2 s); stall: a
+// diagnostic that makes the drain wait on a barrier nobody arrives on, so
+// that every role of the kernel runs into its bound (gcp_debug_timeout).
 int tc_launch_gemm1(const TcOperands* opX, const float* X, float* Sig, void* Sh, void* Sl,
                     int M, int Mp, const void* H, int h_f64, int ldh, double* part, State* st,
-                    int bf16, float split_scale, int* dev_err, cudaStream_t s);
+                    int bf16, float split_scale, float* scratch, cudaStream_t s,
+                    unsigned long long wait_ns = 0, int stall = 0);
 int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X, const float* Sig,
                     float* Xn, void* Xnh, void* Xnl, int M, int Mp, State* st, int bf16,
-                    float split_scale, int* dev_err, cudaStream_t s);
+                    float split_scale, float* scratch, cudaStream_t s);
 void tc_set_smem_attrs();
 // Refinement step (FP64): Dn = S - 2 Z - a (S - D) with Z = X D from the
 // fp16 halves of X = S - D (opX, row i scaled by xscale_i) and of D (opD,
@@ -186,14 +194,15 @@ void tc_set_smem_attrs();
 // McWeeny step).
 int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const double* S64,
                         const double* D64, double* Dn64, const double* xscale,
-                        const double* dscale, int M, int Mp, State* st, cudaStream_t s);
+                        const double* dscale, int M, int Mp, State* st, float* scratch,
+                        cudaStream_t s);
 // W = D1^2 - D^2 from the halves of D (opD, scale kRefScale), of
 // Delta = D1 - D (opDelta, scale check_delta_scale(R)) and of Delta at the
 // scale kRefScale (emaps, device maps), and the per-tile partials of
 // D1^2 - D1 = S + W - D1.
 int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void* emaps,
                     const double* S64, const double* D1, double* part, int M, int Mp, State* st,
-                    cudaStream_t s);
+                    float* scratch, cudaStream_t s);
 // Device copies (cudaMalloc'ed, freed with cudaFree) of the hi/lo tensor
 // maps of a pair of Mp x Mp fp16 arrays, for operands named through memory.
 int tc_make_device_maps(void** dev, const void* hi, const void* lo, int Mp, char* err,
@@ -271,6 +280,7 @@ void launch_batch_f64_gemm2(const BatchItem* items, int batch, const int* tile_i
 int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* err, int errlen);
 size_t tc_map_bytes();
 int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
-                         int ntiles, double* part, int bf16, float split_scale, cudaStream_t s);
+                         int ntiles, double* part, int bf16, float split_scale, float* scratch,
+                         cudaStream_t s);
 
 }  // namespace gcp

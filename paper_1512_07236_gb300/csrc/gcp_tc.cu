@@ -16,16 +16,28 @@
 // so B = B^T.  Per K step three MMAs (Ah Bh, Ah Bl, Al Bh) accumulate into
 // one TMEM accumulator (the lo*lo term is below FP32 resolution).
 //
-// Accumulation.  The tensor cores add into their FP32 accumulator with
-// truncation; over a long K that biases every sum toward zero (measured
-// ~6e-5 relative at K = 8192 for same-sign sums).  So the accumulator only
-// ever holds one K chunk of 128 (24 MMAs; 32 in the refinement product):
-// eight drain warps move each chunk from TMEM into FP32 registers with
-// round-to-nearest adds while the MMA warp fills the other of two TMEM
-// buffers.  (Chunks of 64 cost 16% more time in GEMM1 at M = 8192 for no
-// measurable gain in accuracy; longer first chunks of a tile, which would
-// keep the MMAs going through more of the previous tile's epilogue, moved
-// the subspace error past 1e-6 at M = 8192.)
+// Accumulation.  The tensor cores add each MMA (K = 16) into their FP32
+// accumulator with truncation (round toward zero), so the error of a product
+// comes from the MMAs that round at the scale of the accumulated sum, and it
+// rotates the occupied subspace of the final D (noise that does not commute
+// with D is never purified away).  Two measures:
+//   * the accumulator holds one K chunk only (128 for the split products, 32
+//     for the refinement product, whose trace must hold to ~1e-10): eight
+//     drain warps add each chunk into FP32 registers with round-to-nearest
+//     while the MMA warp fills the other of two TMEM buffers (over all of
+//     K = 8192 the truncation biased same-sign sums by ~6e-5 relative;
+//     shorter chunks only trade it for more register adds: 64 and 32 gave
+//     1.13e-6 and 1.49e-6 against 9.9e-7 for the subspace error of the
+//     M = 8192 solve);
+//   * inside a chunk the two cross products (hi x lo, lo x hi: 2^-11 of the
+//     result) are issued first, so they round at their own scale, and only
+//     the hi x hi MMAs round at the scale of the result (one per K step
+//     instead of three): 8.4e-7 against 9.9e-7 at M = 8192.  Both GEMMs of
+//     a step must use the same order (either one alone measured worse than
+//     neither).  A chunk's stages stay resident until its hi x hi pass, so
+//     each stage has separate barriers for its hi and lo halves: the lo
+//     halves are released after the cross pass and refilled early, and only
+//     the hi halves wait for the end of the chunk.
 //
 // GEMM1 (Y = X X).  With S = D^2 = theta^2 J + Sigma, Sigma = 2 theta X + Y,
 // the epilogue writes Sigma (FP32 + halves, exactly symmetric) and per-tile
@@ -41,18 +53,24 @@
 //          (= 2 theta (1-theta)(theta - c) for HPCP).
 //
 // Schedule.  Persistent CTAs (one per SM) walk the 128 x 256 tiles of the
-// upper block triangle.  Three warpgroups: in the first, warp 0 lane 0
-// issues TMA loads (SWIZZLE_64B, 32-wide K blocks, a 4-stage ring of 48 KB
-// stages) and warp 1 lane 0 issues tcgen05.mma (warps 2-3 idle); warps
-// 4-11 drain TMEM and run the epilogue (warp w reads TMEM lanes 32(w%4)..
-// and columns 128((w-4)/4)..).  The first warpgroup hands registers to the
-// other two (setmaxnreg: 40 and 232 a thread against 168 at launch), which
-// hold the 128 x 256 FP32 accumulator, 128 values a thread, without
-// spilling.  Blocks below the diagonal inside a tile are skipped in the
-// epilogue; every element above the diagonal is stored twice (direct and
-// mirrored).  Every wait is bounded
-// (2 s); on expiry the kernel records State::timeout and winds down, still
-// freeing its TMEM.
+// upper block triangle with four warpgroups of specialised warps:
+//   * warpgroup 0: warp 0 lane 0 issues the TMA loads (SWIZZLE_64B, 32-wide
+//     K blocks, a 4-stage ring of 48 KB stages, each in a hi and a lo half),
+//     warp 1 lane 0 the tcgen05.mma;
+//   * warpgroups 1-2, eight drain warps: warp w reads TMEM lanes
+//     32 (w % 4).. and columns 128 ((w - 4) / 4).. of each chunk and keeps
+//     the tile's 128 x 256 FP32 sum in registers (128 a thread); at the end
+//     of a tile they store it to one of two scratch slots of this CTA in
+//     global memory (128 KB each, L2-resident) and start on the next tile;
+//   * warpgroup 3, four epilogue warps: the tile's epilogue from the scratch
+//     slot, rows 32 e.. for warp 12 + e, while the next tile accumulates.
+// So the MMA warp never waits for an epilogue (it waited ~25 % of a tile at
+// M = 8192 when the drain warps also ran the epilogue).  Register budgets
+// (setmaxnreg): 40 / 176 / 120 a thread against 128 at launch.  Blocks
+// below the diagonal are skipped; every element above the diagonal is
+// stored twice (direct and mirrored).  Every wait is bounded (2 s unless the
+// launch asks for less); on expiry the kernel records State::timeout and
+// winds down, still freeing its TMEM.
 #include <cuda.h>
 #include <stdio.h>
 #include <string.h>
@@ -70,31 +88,34 @@ struct TcOperands {
 
 namespace {
 using namespace tcx;
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 4;
-// K chunk per TMEM drain = kc_stages * BK: 128 for the split phase; 32 for
-// the FP64 refinement product (mode 3), whose trace must hold to ~1e-10:
-// the truncation inside a chunk biases the diagonal of (S - D) D toward
-// zero by about (MMAs per chunk) 2^-25, and 24 MMAs per chunk moved
-// Tr D_{n+1} by ~1e-9 at M = 8192.
+constexpr int BM = 128, BN = 256, BK = 32;
+// Operand ring: every 32-wide K block ("stage") has a hi part (A hi, B hi)
+// and a lo part (A lo, B lo) of 24 KB each, in separate rings.  The cross
+// products of a chunk read both, the hi x hi pass at its end only the hi
+// part, so the hi ring has one slot more: the next chunk's first hi part
+// loads while the current chunk is still in its cross pass.
+constexpr int kLoSlots = 4, kHiSlots = 5;
+// K chunk per TMEM drain, in 32-wide K blocks (see the header comment).
 template <int MODE>
 __host__ __device__ constexpr int kc_stages() {
   return MODE == 3 ? 1 : 4;
 }
-constexpr int kThreads = 384;
-constexpr uint32_t kCtlRegs = 40, kDrainRegs = 232;  // per thread, after setmaxnreg
-static_assert(128 * kCtlRegs + 256 * kDrainRegs <= 65536, "register split");
-constexpr uint32_t kABytes = BM * BK * 2;                     // 8 KB
-constexpr uint32_t kBBytes = BN * BK * 2;                     // 16 KB
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
-constexpr uint32_t kTpBytes = 8 * 32 * 32 * 4;  // one 32 x 32 float block per drain warp
-// The split GEMMs' epilogues use the transposition buffers; the refinement
-// product keeps that shared memory as L1 cache for its row-wise FP64 loads.
-template <int MODE>
-__host__ __device__ constexpr uint32_t smem_bytes() {
-  return STAGES * kStageBytes + (MODE == 1 || MODE == 2 ? kTpBytes : 0u) + 1024;
-}
-static_assert(smem_bytes<1>() + 768 <= 227 * 1024, "shared memory per CTA");
+static_assert(4 <= kLoSlots && 4 < kHiSlots, "a chunk must fit the rings");
+constexpr int kThreads = 512;
+constexpr int kEpiWarp0 = 12;  // first epilogue warp
+constexpr int kEpiThreads = 128;
+constexpr int kEpiBarrier = 2;  // named barrier of the epilogue warps
+constexpr uint32_t kCtlRegs = 40, kDrainRegs = 176, kEpiRegs = 120;  // per thread
+static_assert(128 * kCtlRegs + 256 * kDrainRegs + 128 * kEpiRegs <= 65536, "register split");
+constexpr uint32_t kABytes = BM * BK * 2;           // 8 KB
+constexpr uint32_t kBBytes = BN * BK * 2;           // 16 KB
+constexpr uint32_t kPartBytes = kABytes + kBBytes;  // 24 KB: the hi (or lo) part of a stage
+constexpr uint32_t kSmemBytes = (kLoSlots + kHiSlots) * kPartBytes + 1024;
+static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
+// Scratch slot: a finished tile row-major (BM x BN) and transposed (BN x BM).
+constexpr size_t kTileFloats = (size_t)BM * BN;
+constexpr size_t kSlotFloats = 2 * kTileFloats;
 
 struct Epi {
   const float* X;    // current shifted iterate (FP32, Mp x Mp)
@@ -121,6 +142,10 @@ struct Epi {
   // new iterate D1, the product W = D1^2 - D^2 in the scale kRefScale s_Delta;
   // emaps: device maps of Delta at the scale kRefScale (B of the Delta^2 part)
   const CUtensorMap* emaps;
+  // drain -> epilogue hand-over: 2 slots of BM x BN floats per CTA
+  float* scratch;
+  unsigned long long wait_ns;  // bound of every wait
+  int stall;  // diagnostic: the drain first waits on a barrier nobody arrives on
 };
 
 // Linear tile index -> (I, J): I a 128-row block, J a 256-column block,
@@ -148,20 +173,33 @@ __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
   J = 0;
 }
 
-// Refinement-product epilogue of one thread: its row, 128 columns of one
-// 128-block (jb = 2J + half), values acc[] = (A B)_row,c in the slice scale.
+__device__ __forceinline__ void load_row32(const float* __restrict__ src, float (&a)[32]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(src) + k);
+    a[4 * k] = v.x;
+    a[4 * k + 1] = v.y;
+    a[4 * k + 2] = v.z;
+    a[4 * k + 3] = v.w;
+  }
+}
+
+// Refinement-product epilogue of one thread: its row, 32 columns c_base..,
+// acc[] = (A B)_row,c in the slice scale, read from the scratch row `src`.
 // McWeeny refinement step in FP64 (Eq. mcweeny3): with S = D^2 exact and
 // X = S - D small, 3D^2 - 2D^3 = S - 2 X D; the product Z = X D only needs
 // the relative accuracy of the split product because |X| is small.  The
 // general step of Eq. hpcp3 is the same plus (1 - 2c)(D - S); the control
 // kernel sets c within 1/2 +- 0.05 to put Tr D+ back at N.
-__device__ __forceinline__ void refine_row(const Epi& ep, int row, int c_base, bool diag_blk,
-                                           const float (&acc)[128]) {
+__device__ __forceinline__ void refine_seg(const Epi& ep, int row, int c_base, bool diag_blk,
+                                           const float* __restrict__ src) {
   if (row >= ep.M) return;
+  float acc[32];
+  load_row32(src, acc);
   const double wr = 1.0 / (kRefScale * ep.rs_x[row]);  // powers of two: exact
   const double g = ep.st->a;
 #pragma unroll
-  for (int k = 0; k < 128; ++k) {
+  for (int k = 0; k < 32; ++k) {
     const int c = c_base + k;
     if (c >= ep.M || (diag_blk && c < row)) continue;
     const size_t o = (size_t)row * ep.ld64 + c;
@@ -178,13 +216,14 @@ __device__ __forceinline__ void refine_row(const Epi& ep, int row, int c_base, b
 // formed in FP64 (S and D1 are O(1), the result is ~R1).  Sums: the
 // residual R1^2 (FP32 per lane, weight 2 above the diagonal), Tr D1 and
 // Tr D1^2 = Tr S + Tr W (FP64, diagonal only).
-__device__ __forceinline__ void check_row(const Epi& ep, int row, int c_base, bool diag_blk,
-                                          const float (&acc)[128], float inv_scale,
-                                          float (&pp)[3], double (&dpart)[5]) {
+__device__ __forceinline__ void check_seg(const Epi& ep, int row, int c_base, bool diag_blk,
+                                          const float* __restrict__ src, float inv_scale,
+                                          float (&pp)[3], double (&dpart)[2]) {
   if (row >= ep.M) return;
-  // fully unrolled: acc[] stays in registers
+  float acc[32];
+  load_row32(src, acc);
 #pragma unroll
-  for (int k = 0; k < 128; ++k) {
+  for (int k = 0; k < 32; ++k) {
     const int c = c_base + k;
     if (c >= ep.M || (diag_blk && c < row)) continue;
     const size_t o = (size_t)row * ep.ld64 + c;
@@ -197,22 +236,6 @@ __device__ __forceinline__ void check_row(const Epi& ep, int row, int c_base, bo
       dpart[1] += sw;
     }
   }
-}
-
-// GEMM1 epilogue of one warp for one 32 x 32 block: rows row0..row0+31,
-// columns c0..c0+31; the caller has written s^2 (X X)_{row0+lane, c0+k} to
-// row `lane` of the warp's shared buffer `tp` (lane = row, as the
-// accumulator comes out of TMEM; 4-float groups XOR-swizzled by row), and
-// the block is read back with eight lanes per row and four consecutive
-// columns per lane, so that the X loads and the direct stores of Sigma and
-// its halves are whole 128-byte row segments; Sigma goes back to `tp` and
-// the mirrored stores read it with eight lanes per column.
-// Blocks on the diagonal take an element-wise path (upper triangle only).
-// The XOR key (r ^ r >> 2) & 7 takes eight distinct values over any eight
-// consecutive rows (float4 rows written by lanes = rows) and over rows
-// 4g + i, g = 0..7 (the mirrored reads): both are conflict-free.
-__device__ __forceinline__ int tp_idx(int r, int c) {
-  return r * 32 + ((((c >> 2) ^ ((r ^ (r >> 2)) & 7)) << 2) | (c & 3));
 }
 
 template <bool BF16>
@@ -238,197 +261,150 @@ __device__ __forceinline__ void store_out1(const Epi& ep, size_t off, float o) {
   reinterpret_cast<HT*>(ep.out_l)[off] = l;
 }
 
-template <bool BF16>
-__device__ __forceinline__ void gemm1_block(const Epi& ep, int row0, int c0, bool diag_blk,
-                                            float thf, float f2th, float thtb, float (&pp)[3],
-                                            double (&dpart)[5], float* tp) {
-  const int lane = threadIdx.x & 31;
-  const int Mp = ep.Mp;
-  const float is2 = ep.inv_s2;
-  __syncwarp();
-  if (!diag_blk) {
-    // every element lies above the diagonal (weight 2, mirrored)
-    const int rs = lane >> 3, cl = 4 * (lane & 7);
-    const size_t cbase = (size_t)c0 + cl;
-    // all eight X loads in flight before the first store (loads issued
-    // after stores queue behind them)
-    float4 xx[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      xx[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(row0 + rs + 4 * j) * Mp + cbase);
-#pragma unroll
-    for (int jh = 0; jh < 8; jh += 4) {
-      const float4* x = xx + jh;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int rr = rs + 4 * (jh + j);
-        const size_t off = (size_t)(row0 + rr) * Mp + cbase;
-        const float4 a = *reinterpret_cast<const float4*>(&tp[tp_idx(rr, cl)]);
-        float4 o;
-        o.x = fmaf(f2th, x[j].x, a.x * is2);  // Sigma = 2 theta X + Y
-        o.y = fmaf(f2th, x[j].y, a.y * is2);
-        o.z = fmaf(f2th, x[j].z, a.z * is2);
-        o.w = fmaf(f2th, x[j].w, a.w * is2);
-        const float ex = o.x - x[j].x, ey = o.y - x[j].y, ez = o.z - x[j].z, ew = o.w - x[j].w;
-        pp[0] += 2.f * (o.x * x[j].x + o.y * x[j].y + o.z * x[j].z + o.w * x[j].w);
-        pp[1] += 2.f * (ex * ex + ey * ey + ez * ez + ew * ew);
-        if (ep.H) {
-          const int r = row0 + rr;
-          const float xs[4] = {x[j].x, x[j].y, x[j].z, x[j].w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int cc = c0 + cl + i;
-            if (r < ep.M && cc < ep.M) {
-              const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + cc]
-                                        : (double)((const float*)ep.H)[(size_t)r * ep.ldh + cc];
-              pp[2] += 2.f * xs[i] * (float)h;
-            }
-          }
-        }
-        store_out4<BF16>(ep, off, o);
-        *reinterpret_cast<float4*>(&tp[tp_idx(rr, cl)]) = o;
-      }
-    }
-    __syncwarp();
-    // mirror: eight lanes per original column, four consecutive rows each
-    const int cs = lane >> 3, gr = lane & 7;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int cc = cs + 4 * j;
-      const float4 m = make_float4(tp[tp_idx(4 * gr, cc)], tp[tp_idx(4 * gr + 1, cc)],
-                                   tp[tp_idx(4 * gr + 2, cc)], tp[tp_idx(4 * gr + 3, cc)]);
-      store_out4<BF16>(ep, (size_t)(c0 + cc) * Mp + row0 + 4 * gr, m);
-    }
-    __syncwarp();
-  } else {
-    // diagonal block: lane = column, element (row0 + k, c0 + lane)
-    const int c = c0 + lane;
-    float o[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const int r = row0 + k;
-      const bool keep = c >= r;
-      const bool on_diag = c == r && r < ep.M;
-      const size_t off = (size_t)r * Mp + c;
-      const float a = tp[tp_idx(k, lane)];
-      const float x = ep.X[off];
-      const float sg = fmaf(f2th, x, a * is2);
-      // weight: an element above the diagonal stands for its mirror too
-      const float w = keep ? (c == r ? 1.f : 2.f) : 0.f;
-      const float e = sg - x - (on_diag ? thtb : 0.f);  // (S - D)_rc
-      pp[0] += w * sg * x;
-      pp[1] += w * e * e;
-      if (on_diag) {
-        dpart[0] += (double)x;
-        dpart[1] += (double)sg;
-      }
-      if (ep.H && r < ep.M && c < ep.M) {
-        const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + c]
-                                  : (double)((const float*)ep.H)[(size_t)r * ep.ldh + c];
-        const float d = x + (on_diag ? thf : 0.f);
-        pp[2] += w * d * (float)h;
-      }
-      o[k] = sg;
-      if (keep) store_out1<BF16>(ep, off, sg);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 32; ++k) tp[tp_idx(k, lane)] = o[k];
-    __syncwarp();
-    const int r = row0 + lane;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const int cc = c0 + k;
-      if (cc <= r) continue;
-      store_out1<BF16>(ep, (size_t)cc * Mp + r, tp[tp_idx(lane, k)]);
-    }
-    __syncwarp();
-  }
-}
+// The epilogues of the split GEMMs work on 32 x 32 blocks of the output with
+// eight lanes per row and four consecutive columns per lane, so every load
+// and store is a whole 128-byte row segment.  A block above the diagonal is
+// written twice: the direct pass (rows r, columns c) reads the product from
+// the row-major scratch tile, the mirror pass (rows c, columns r) from the
+// transposed copy the drain warps wrote.  The mirror pass recomputes each
+// value from the same inputs (X and Sigma are stored exactly symmetric), so
+// the two stores are bitwise equal, without a shared-memory transpose.  On a
+// diagonal block the direct pass keeps the elements on or above the
+// diagonal and the mirror pass those strictly below.
 
-// The epilogues run once per tile, so their code is fetched cold every
-// time: each keeps one copy of its block body in a runtime loop over the
-// four 32-column blocks and moves the block's accumulator registers to
-// shared memory with this (a switch over the block gives every case
-// compile-time register indices).
-template <int P>
-__device__ __forceinline__ void acc_to_tp(const float (&acc)[128], float* tp, int lane) {
-#pragma unroll
-  for (int g = 0; g < 8; ++g)
-    *reinterpret_cast<float4*>(&tp[tp_idx(lane, 4 * g)]) =
-        make_float4(acc[32 * P + 4 * g], acc[32 * P + 4 * g + 1], acc[32 * P + 4 * g + 2],
-                    acc[32 * P + 4 * g + 3]);
-}
-// GEMM2 epilogue of one warp for one 32 x 32 block, laid out as in
-// gemm1_block (the caller has written s^2 (X Sigma)_{row0+lane, c0+k} to
-// row `lane` of `tp`): X_{n+1} = ca X + cb Sigma + cz Z (+ cj on the
-// diagonal of the unpadded block) is formed with eight lanes per row, so the
-// X and Sigma loads and the stores are whole row segments.  In a block of
-// the diagonal 128-block only elements on or above the diagonal are stored
-// (element-wise), those above it mirrored.  Without products (mma false)
-// the block is a copy of X.
-template <bool BF16>
-__device__ __forceinline__ void gemm2_block(const Epi& ep, int row0, int c0, bool diag_blk,
-                                            bool mma, float ca, float cb, float cj, float cz,
-                                            float* tp) {
+// GEMM1 epilogue of one warp for one 32 x 32 block: output rows orow0..,
+// columns ocol0..; `yb` points at s^2 (X X) for the block's first element in
+// the scratch tile, row stride ys.  Sigma = 2 theta X + Y and its halves are
+// stored; the direct pass (MIRROR false) also accumulates the partial sums.
+template <bool BF16, bool MIRROR>
+__device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restrict__ yb, int ys,
+                                           int orow0, int ocol0, bool diag_blk, float thf,
+                                           float f2th, float thtb, float (&pp)[3],
+                                           double (&dpart)[2]) {
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
   const int rs = lane >> 3, cl = 4 * (lane & 7);
-  const size_t cbase = (size_t)c0 + cl;
-  float4 xx[8], ss[8];
+  const size_t cbase = (size_t)ocol0 + cl;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const size_t off = (size_t)(row0 + rs + 4 * j) * Mp + cbase;
-    xx[j] = *reinterpret_cast<const float4*>(ep.X + off);
-    ss[j] = *reinterpret_cast<const float4*>(ep.Sig + off);
-  }
-  __syncwarp();
+  for (int jh = 0; jh < 8; jh += 4) {
+    // the block's loads in flight before its first store
+    float4 xx[4], yy[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int rr = rs + 4 * j;
-    const size_t off = (size_t)(row0 + rr) * Mp + cbase;
-    const float4 a = *reinterpret_cast<const float4*>(&tp[tp_idx(rr, cl)]);
-    float4 o = xx[j];
-    if (mma) {
-      o.x = fmaf(ca, xx[j].x, fmaf(cb, ss[j].x, cz * (a.x * is2)));
-      o.y = fmaf(ca, xx[j].y, fmaf(cb, ss[j].y, cz * (a.y * is2)));
-      o.z = fmaf(ca, xx[j].z, fmaf(cb, ss[j].z, cz * (a.z * is2)));
-      o.w = fmaf(ca, xx[j].w, fmaf(cb, ss[j].w, cz * (a.w * is2)));
+    for (int j = 0; j < 4; ++j) {
+      const int rr = rs + 4 * (jh + j);
+      xx[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(orow0 + rr) * Mp + cbase);
+      yy[j] = __ldcg(reinterpret_cast<const float4*>(yb + rr * ys + cl));
     }
-    if (!diag_blk) {
-      store_out4<BF16>(ep, off, o);
-    } else {
-      const int r = row0 + rr;
-      float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int c = c0 + cl + i;
-        if (mma && c == r && r < ep.M) ov[i] += cj;
-        if (c >= r) store_out1<BF16>(ep, off + i, ov[i]);
+    for (int j = 0; j < 4; ++j) {
+      const int r = orow0 + rs + 4 * (jh + j);
+      const size_t off = (size_t)r * Mp + cbase;
+      float4 o;
+      o.x = fmaf(f2th, xx[j].x, yy[j].x * is2);  // Sigma = 2 theta X + Y
+      o.y = fmaf(f2th, xx[j].y, yy[j].y * is2);
+      o.z = fmaf(f2th, xx[j].z, yy[j].z * is2);
+      o.w = fmaf(f2th, xx[j].w, yy[j].w * is2);
+      if (!diag_blk) {
+        if (!MIRROR) {
+          // every element lies above the diagonal (weight 2: it stands for
+          // its mirror too)
+          const float ex = o.x - xx[j].x, ey = o.y - xx[j].y, ez = o.z - xx[j].z,
+                      ew = o.w - xx[j].w;
+          pp[0] += 2.f * (o.x * xx[j].x + o.y * xx[j].y + o.z * xx[j].z + o.w * xx[j].w);
+          pp[1] += 2.f * (ex * ex + ey * ey + ez * ez + ew * ew);
+        }
+        store_out4<BF16>(ep, off, o);
+      } else {
+        const float xs[4] = {xx[j].x, xx[j].y, xx[j].z, xx[j].w};
+        const float os[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = ocol0 + cl + i;
+          if (MIRROR ? (c >= r) : (c < r)) continue;
+          if (!MIRROR) {
+            const bool on_diag = c == r && r < ep.M;
+            const float w = c == r ? 1.f : 2.f;
+            const float e = os[i] - xs[i] - (on_diag ? thtb : 0.f);  // (S - D)_rc
+            pp[0] += w * os[i] * xs[i];
+            pp[1] += w * e * e;
+            if (on_diag) {
+              dpart[0] += (double)xs[i];
+              dpart[1] += (double)os[i];
+            }
+          }
+          store_out1<BF16>(ep, off + i, os[i]);
+        }
       }
-      o = make_float4(ov[0], ov[1], ov[2], ov[3]);
-    }
-    *reinterpret_cast<float4*>(&tp[tp_idx(rr, cl)]) = o;
-  }
-  __syncwarp();
-  const int cs = lane >> 3, gr = lane & 7;
+      if (!MIRROR && ep.H) {
+        const float xs[4] = {xx[j].x, xx[j].y, xx[j].z, xx[j].w};
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int cc = cs + 4 * j;
-    const float4 m = make_float4(tp[tp_idx(4 * gr, cc)], tp[tp_idx(4 * gr + 1, cc)],
-                                 tp[tp_idx(4 * gr + 2, cc)], tp[tp_idx(4 * gr + 3, cc)]);
-    const size_t mo = (size_t)(c0 + cc) * Mp + row0 + 4 * gr;
-    if (!diag_blk) {
-      store_out4<BF16>(ep, mo, m);
-    } else {
-      const float mv[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (c0 + cc > row0 + 4 * gr + i) store_out1<BF16>(ep, mo + i, mv[i]);
+        for (int i = 0; i < 4; ++i) {
+          const int cc = ocol0 + cl + i;
+          if (r < ep.M && cc < ep.M && (!diag_blk || cc >= r)) {
+            const double h = ep.h_f64 ? ((const double*)ep.H)[(size_t)r * ep.ldh + cc]
+                                      : (double)((const float*)ep.H)[(size_t)r * ep.ldh + cc];
+            const float d = xs[i] + (cc == r ? thf : 0.f);
+            pp[2] += (cc == r ? 1.f : 2.f) * d * (float)h;
+          }
+        }
+      }
     }
   }
-  __syncwarp();
+}
+
+// GEMM2 epilogue of one warp for one 32 x 32 block, laid out as gemm1_pass
+// (`yb`: s^2 (X Sigma) in the scratch tile): X_{n+1} = ca X + cb Sigma +
+// cz Z (+ cj on the diagonal of the unpadded block).  Without products (mma
+// false) the block is a copy of X and `yb` is not read.
+template <bool BF16, bool MIRROR>
+__device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restrict__ yb, int ys,
+                                           int orow0, int ocol0, bool diag_blk, bool mma,
+                                           float ca, float cb, float cj, float cz) {
+  const int lane = threadIdx.x & 31;
+  const int Mp = ep.Mp;
+  const float is2 = ep.inv_s2;
+  const int rs = lane >> 3, cl = 4 * (lane & 7);
+  const size_t cbase = (size_t)ocol0 + cl;
+  // two rows in flight per lane (three float4 operands each)
+#pragma unroll
+  for (int jh = 0; jh < 8; jh += 2) {
+    float4 xx[2], ss[2], yy[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int rr = rs + 4 * (jh + j);
+      const size_t off = (size_t)(orow0 + rr) * Mp + cbase;
+      xx[j] = *reinterpret_cast<const float4*>(ep.X + off);
+      if (mma) {
+        ss[j] = *reinterpret_cast<const float4*>(ep.Sig + off);
+        yy[j] = __ldcg(reinterpret_cast<const float4*>(yb + rr * ys + cl));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = orow0 + rs + 4 * (jh + j);
+      const size_t off = (size_t)r * Mp + cbase;
+      float4 o = xx[j];
+      if (mma) {
+        o.x = fmaf(ca, xx[j].x, fmaf(cb, ss[j].x, cz * (yy[j].x * is2)));
+        o.y = fmaf(ca, xx[j].y, fmaf(cb, ss[j].y, cz * (yy[j].y * is2)));
+        o.z = fmaf(ca, xx[j].z, fmaf(cb, ss[j].z, cz * (yy[j].z * is2)));
+        o.w = fmaf(ca, xx[j].w, fmaf(cb, ss[j].w, cz * (yy[j].w * is2)));
+      }
+      if (!diag_blk) {
+        store_out4<BF16>(ep, off, o);
+      } else {
+        const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = ocol0 + cl + i;
+          if (MIRROR ? (c >= r) : (c < r)) continue;
+          const float v = (!MIRROR && mma && c == r && r < ep.M) ? ov[i] + cj : ov[i];
+          store_out1<BF16>(ep, off + i, v);
+        }
+      }
+    }
+  }
 }
 
 // Everything one tile needs: its block coordinates, operand maps, the
@@ -524,28 +500,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (st->stopped || st->timeout) return;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int KC = kc_stages<MODE>();
 
-  __shared__ __align__(8) uint64_t full_bar[STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t accf_bar[2];
-  __shared__ __align__(8) uint64_t acce_bar[2];
+  // each stage has two halves, the hi operands and the lo operands, with a
+  // full and an empty barrier each: the lo halves are needed only by the
+  // cross products, so they are released (and refilled) ahead of the hi
+  // halves, which the hi x hi pass at the end of the chunk still reads
+  __shared__ __align__(8) uint64_t full_hi[kHiSlots], full_lo[kLoSlots];
+  __shared__ __align__(8) uint64_t empty_hi[kHiSlots], empty_lo[kLoSlots];
+  __shared__ __align__(8) uint64_t accf_bar[2];    // chunk in TMEM buffer b complete
+  __shared__ __align__(8) uint64_t acce_bar[2];    // TMEM buffer b drained
+  __shared__ __align__(8) uint64_t sfull_bar[2];   // scratch slot holds a finished tile
+  __shared__ __align__(8) uint64_t sempty_bar[2];  // scratch slot consumed by the epilogue
   __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ __align__(8) uint64_t never_bar;      // no thread arrives on it (diagnostic)
   __shared__ uint32_t tmem_holder;
-  __shared__ double red[2 * 8 * 5];
+  __shared__ double red[2 * 4 * 5];
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+    for (int s = 0; s < kHiSlots; ++s) {
+      mbar_init(&full_hi[s], 1);
+      mbar_init(&empty_hi[s], 1);
+    }
+    for (int s = 0; s < kLoSlots; ++s) {
+      mbar_init(&full_lo[s], 1);
+      mbar_init(&empty_lo[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
-      mbar_init(&acce_bar[b], kDrainThreads / 32);
+      mbar_init(&acce_bar[b], 8);               // the eight drain warps
+      mbar_init(&sfull_bar[b], 8);              // the eight drain warps
+      mbar_init(&sempty_bar[b], kEpiThreads / 32);  // the four epilogue warps
     }
     mbar_init(&fin_bar, 1);
+    mbar_init(&never_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -559,25 +550,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
   int* timeout_flag = BATCHED ? &items[0].st->timeout : &ep.st->timeout;
+  const unsigned long long wlim = ep.wait_ns;
 
   if (warp < 4) {
     reg_dealloc<kCtlRegs>();
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
-      uint32_t g = 0;  // global stage counter
+      // Stage by stage, the lo part then the hi part (ring slots gs % kLoSlots
+      // and gs % kHiSlots for global stage gs).
+      uint32_t gs = 0;              // global stage counter
+      uint32_t issued[2] = {0, 0};  // parts issued so far: lo, hi
       bool alive = true;
       for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
         TileCtx c;
         make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
-        for (int kb = 0; kb < c.nkb; ++kb, ++g) {
-          const uint32_t s = g % STAGES;
-          if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1)) {
-            atomicOr(timeout_flag, 1);
-            alive = false;
-            break;
-          }
-          const uint32_t stage = sbase + s * kStageBytes;
-          mbar_expect_tx(&full_bar[s], kStageBytes);
+        for (int kb = 0; kb < c.nkb && alive; ++kb, ++gs) {
           int kx = kb * BK;
           const CUtensorMap *ah = c.ah, *al = c.al, *bh = c.bh, *bl = c.bl;
           if (MODE == 4) {
@@ -598,19 +585,38 @@ __global__ void __launch_bounds__(kThreads, 1)
               bl = &c.ep.emaps[1];
             }
           }
-          tma_load_2d(ah, &full_bar[s], stage, kx, c.I * BM);
-          tma_load_2d(al, &full_bar[s], stage + kABytes, kx, c.I * BM);
-          tma_load_2d(bh, &full_bar[s], stage + 2 * kABytes, kx, c.J * BN);
-          tma_load_2d(bh, &full_bar[s], stage + 2 * kABytes + kBBytes / 2, kx, c.J * BN + 128);
-          tma_load_2d(bl, &full_bar[s], stage + 2 * kABytes + kBBytes, kx, c.J * BN);
-          tma_load_2d(bl, &full_bar[s], stage + 2 * kABytes + kBBytes + kBBytes / 2, kx,
-                      c.J * BN + 128);
+          for (int hi = 0; hi < 2; ++hi) {
+            const int nsl = hi ? kHiSlots : kLoSlots;
+            const uint32_t sl = gs % nsl, use = gs / nsl;
+            uint64_t* emp = hi ? &empty_hi[sl] : &empty_lo[sl];
+            uint64_t* ful = hi ? &full_hi[sl] : &full_lo[sl];
+            if (use >= 1 && !mbar_wait(emp, (use - 1) & 1, wlim)) {
+              atomicOr(timeout_flag, 1);
+              alive = false;
+              break;
+            }
+            const uint32_t dst = sbase + (hi ? sl : kHiSlots + sl) * kPartBytes;
+            const CUtensorMap* am = hi ? ah : al;
+            const CUtensorMap* bm = hi ? bh : bl;
+            mbar_expect_tx(ful, kPartBytes);
+            tma_load_2d(am, ful, dst, kx, c.I * BM);
+            tma_load_2d(bm, ful, dst + kABytes, kx, c.J * BN);
+            tma_load_2d(bm, ful, dst + kABytes + kBBytes / 2, kx, c.J * BN + 128);
+            issued[hi] = gs + 1;
+          }
+          if (!alive) break;
         }
       }
-      // every issued load must land before the CTA exits
-      const uint32_t first = g > STAGES ? g - STAGES : 0;
-      for (uint32_t k = first; k < g; ++k)
-        if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(timeout_flag, 1);
+      // every issued load must land before the CTA exits: the last uses of
+      // each ring (earlier ones were waited on by the MMA warp before it
+      // released their slots)
+      for (int hi = 0; hi < 2; ++hi) {
+        const uint32_t nsl = hi ? kHiSlots : kLoSlots;
+        uint64_t* ful = hi ? full_hi : full_lo;
+        const uint32_t n = issued[hi], first = n > nsl ? n - nsl : 0;
+        for (uint32_t k = first; k < n; ++k)
+          if (!mbar_wait(&ful[k % nsl], (k / nsl) & 1, wlim)) atomicOr(timeout_flag, 1);
+      }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = idesc_f16(BF16 ? 1 : 0);
@@ -619,74 +625,90 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
         TileCtx c;
         make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
-        const int nchunk = c.nkb / kc_stages<MODE>();
+        const int nchunk = c.nkb / KC;
         for (int ch = 0; ch < nchunk && alive; ++ch, ++qc) {
           const uint32_t b = qc & 1;
-          if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1)) {
+          if (qc >= 2 && !mbar_wait(&acce_bar[b], ((qc >> 1) - 1) & 1, wlim)) {
             atomicOr(timeout_flag, 1);
             alive = false;
             break;
           }
           tc_fence_after();
           const uint32_t acc = tmem + b * 256;
-          for (int ks = 0; ks < kc_stages<MODE>(); ++ks, ++g) {
-            const uint32_t s = g % STAGES;
-            if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
+          // the cross products of the chunk first (they round at their own
+          // scale), releasing each stage's lo part; then hi x hi, releasing
+          // the hi parts
+          for (int ks = 0; ks < KC; ++ks) {
+            const uint32_t gs = g + ks, sl = gs % kLoSlots, sh = gs % kHiSlots;
+            if (!mbar_wait(&full_lo[sl], (gs / kLoSlots) & 1, wlim) ||
+                !mbar_wait(&full_hi[sh], (gs / kHiSlots) & 1, wlim)) {
               atomicOr(timeout_flag, 1);
               alive = false;
               break;
             }
             tc_fence_after();
-            const uint32_t a_h = sbase + s * kStageBytes;
-            const uint32_t a_l = a_h + kABytes;
-            const uint32_t b_h = a_h + 2 * kABytes;
-            const uint32_t b_l = b_h + kBBytes;
+            const uint32_t a_h = sbase + sh * kPartBytes, b_h = a_h + kABytes;
+            const uint32_t a_l = sbase + (kHiSlots + sl) * kPartBytes, b_l = a_l + kABytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 halves = 32 B inside the 64 B swizzle row
-              const uint32_t first = (ks == 0 && kk == 0) ? 0u : 1u;
-              umma(acc, sdesc(a_h + off), sdesc(b_h + off), idesc, first);
-              umma(acc, sdesc(a_h + off), sdesc(b_l + off), idesc, 1u);
+              umma(acc, sdesc(a_h + off), sdesc(b_l + off), idesc, (ks == 0 && kk == 0) ? 0u : 1u);
               umma(acc, sdesc(a_l + off), sdesc(b_h + off), idesc, 1u);
             }
-            umma_commit(&empty_bar[s]);
+            umma_commit(&empty_lo[sl]);
           }
+          if (!alive) break;
+          for (int ks = 0; ks < KC; ++ks) {
+            const uint32_t sh = (g + ks) % kHiSlots;
+            const uint32_t a_h = sbase + sh * kPartBytes, b_h = a_h + kABytes;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              umma(acc, sdesc(a_h + off), sdesc(b_h + off), idesc, 1u);
+            }
+            umma_commit(&empty_hi[sh]);
+          }
+          g += KC;
           umma_commit(&accf_bar[b]);
         }
       }
       // every MMA issued here must be complete before TMEM is freed
       umma_commit(&fin_bar);
-      if (!mbar_wait(&fin_bar, 0)) atomicOr(timeout_flag, 1);
+      if (!mbar_wait(&fin_bar, 0, wlim)) atomicOr(timeout_flag, 1);
     }
-  } else {
+  } else if (warp < kEpiWarp0) {
     reg_alloc<kDrainRegs>();
-    // ---------------- drain + epilogue (warps 4..11) ----------------
+    // ---------------- drain (warps 4..11) ----------------
     // TMEM lane quarter is fixed by the warp's rank within its warpgroup
     const int dw = warp - 4, q = warp & 3, half = dw >> 2;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    float* tp = reinterpret_cast<float*>(smem_raw + (sbase - raw) + STAGES * kStageBytes) +
-                dw * 32 * 32;
-    uint32_t qc = 0, nred = 0;
+    float* slots = ep.scratch + (size_t)blockIdx.x * 2 * kSlotFloats;
+    uint32_t qc = 0, u = 0;
     bool alive = true;
-    for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
+    if (ep.stall) {
+      // diagnostic: a wait that no thread will satisfy, to exercise the
+      // bounded-wait path of every role (see gcp_debug_timeout)
+      if (!__all_sync(0xffffffffu, mbar_wait(&never_bar, 0, wlim))) {
+        if (lane == 0) atomicOr(timeout_flag, 1);
+        alive = false;
+      }
+    }
+    for (int t = blockIdx.x; t < ep.ntiles && alive; t += gridDim.x) {
       TileCtx c;
       make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
-      if (c.skip) continue;  // uniform over the CTA
+      if (c.skip || c.nkb == 0) continue;  // no products: nothing to hand over
       float acc[128];
 #pragma unroll
       for (int k = 0; k < 128; ++k) acc[k] = 0.f;
-      const int nchunk = c.nkb / kc_stages<MODE>();
+      const int nchunk = c.nkb / KC;
       for (int ch = 0; ch < nchunk; ++ch, ++qc) {
         const uint32_t b = qc & 1;
-        if (alive) {
-          // warp-uniform: tcgen05.ld below is a warp-collective instruction
-          const bool got = __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1));
-          if (!got) {
-            if (lane == 0) atomicOr(timeout_flag, 1);
-            alive = false;
-          }
+        // warp-uniform: tcgen05.ld below is a warp-collective instruction
+        if (!__all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (qc >> 1) & 1, wlim))) {
+          if (lane == 0) atomicOr(timeout_flag, 1);
+          alive = false;
+          break;
         }
-        if (!alive) break;
         tc_fence_after();
         const uint32_t base = tmem + lane_base + b * 256 + half * 128;
 #pragma unroll
@@ -701,80 +723,155 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[b]);
       }
-      // all drain warps agree on whether the tile completed
-      drain_bar_sync();
-      const bool ok = alive && !(*(volatile int*)timeout_flag);
-      // GEMM1 partials: element sums in FP32 (per lane, then a float shuffle
-      // tree), the diagonal sums Tr X, Tr Sigma in FP64 (dpart[0..1])
-      double dpart[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      float pp[3] = {0.f, 0.f, 0.f};
-      const int jb = 2 * c.J + half;
-      if (ok && jb >= c.I) {
-        if constexpr (MODE == 1) {
-          const double th = c.ep.st->theta;
-          const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
-#pragma unroll 1
-          for (int part = 0; part < 4; ++part) {
-            switch (part) {
-              case 0: acc_to_tp<0>(acc, tp, lane); break;
-              case 1: acc_to_tp<1>(acc, tp, lane); break;
-              case 2: acc_to_tp<2>(acc, tp, lane); break;
-              default: acc_to_tp<3>(acc, tp, lane); break;
-            }
-            gemm1_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
-                              jb == c.I, thf, f2th, thtb, pp, dpart, tp);
+      if (!alive) break;
+      // hand the tile to the epilogue warps through scratch slot u & 1
+      const uint32_t slot = u & 1;
+      if (u >= 2 && !__all_sync(0xffffffffu, mbar_wait(&sempty_bar[slot], ((u >> 1) - 1) & 1, wlim))) {
+        if (lane == 0) atomicOr(timeout_flag, 1);
+        alive = false;
+        break;
+      }
+      // row-major (a thread's 128 columns of its row) and transposed (for a
+      // column k the lanes write 32 consecutive rows: 128-byte segments)
+      float* tile = slots + slot * kSlotFloats;
+      float4* dst = reinterpret_cast<float4*>(tile + (size_t)(32 * q + lane) * BN + half * 128);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        __stcg(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
+      // transposed: the four lanes of a quad hold four consecutive rows; a
+      // 4 x 4 transpose across the quad (two xor-shuffle stages) gives lane
+      // 4 m + p column 4 j + p of those rows, stored as one float4
+      const int p4 = lane & 3;
+      float* tq = tile + kTileFloats + (size_t)(half * 128) * BM + 32 * q + (lane & ~3);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float v0 = acc[4 * j], v1 = acc[4 * j + 1], v2 = acc[4 * j + 2], v3 = acc[4 * j + 3];
+        // stage 1 (partner lane ^ 1): swap the off-diagonal 1 x 1 pairs
+        {
+          const bool odd = p4 & 1;
+          const float s0 = odd ? v0 : v1, s1 = odd ? v2 : v3;
+          const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+          const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+          if (odd) {
+            v0 = r0;
+            v2 = r1;
+          } else {
+            v1 = r0;
+            v3 = r1;
           }
-        } else if constexpr (MODE == 2) {
-#pragma unroll 1
-          for (int part = 0; part < 4; ++part) {
-            switch (part) {
-              case 0: acc_to_tp<0>(acc, tp, lane); break;
-              case 1: acc_to_tp<1>(acc, tp, lane); break;
-              case 2: acc_to_tp<2>(acc, tp, lane); break;
-              default: acc_to_tp<3>(acc, tp, lane); break;
-            }
-            gemm2_block<BF16>(c.ep, c.I * BM + 32 * q, c.J * BN + half * 128 + part * 32,
-                              jb == c.I, c.mma, c.ca, c.cb, c.cj, c.cz, tp);
+        }
+        // stage 2 (partner lane ^ 2): swap the off-diagonal 2 x 2 blocks
+        {
+          const bool up = p4 & 2;
+          const float s0 = up ? v0 : v2, s1 = up ? v1 : v3;
+          const float r0 = __shfl_xor_sync(0xffffffffu, s0, 2);
+          const float r1 = __shfl_xor_sync(0xffffffffu, s1, 2);
+          if (up) {
+            v0 = r0;
+            v1 = r1;
+          } else {
+            v2 = r0;
+            v3 = r1;
           }
-        } else if constexpr (MODE == 4) {
-          const float inv = (float)(1.0 / (kRefScale * check_delta_scale(c.ep.st->R)));
-          check_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc, inv,
-                    pp, dpart);
-        } else {
-          refine_row(c.ep, c.I * BM + 32 * q + lane, c.J * BN + half * 128, jb == c.I, acc);
+        }
+        __stcg(reinterpret_cast<float4*>(tq + (size_t)(4 * j + p4) * BM), make_float4(v0, v1, v2, v3));
+      }
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sfull_bar[slot]);
+      ++u;
+    }
+  } else {
+    reg_dealloc<kEpiRegs>();
+    // ---------------- epilogue (warps 12..15) ----------------
+    const int e = warp - kEpiWarp0;  // rows 32 e .. 32 e + 31 of every tile
+    const float* slots = ep.scratch + (size_t)blockIdx.x * 2 * kSlotFloats;
+    uint32_t u = 0, nred = 0;
+    for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
+      TileCtx c;
+      make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
+      if (c.skip) continue;  // uniform over the CTA
+      const bool has = c.nkb > 0;
+      const uint32_t slot = u & 1;
+      bool ok = !(*(volatile int*)timeout_flag);
+      if (has && ok) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&sfull_bar[slot], (u >> 1) & 1, wlim));
+        if (!ok && lane == 0) atomicOr(timeout_flag, 1);
+      }
+      const float* tile = slots + slot * kSlotFloats;
+      double dpart[2] = {0.0, 0.0};  // diagonal sums (FP64)
+      float pp[3] = {0.f, 0.f, 0.f};  // element sums (FP32 per lane)
+      const int row0 = c.I * BM + 32 * e;
+      // does the tile reach the diagonal? (uniform: decides the FP64 sums)
+      const bool tile_diag = (2 * c.J == c.I) || (2 * c.J + 1 == c.I);
+      if (ok) {
+#pragma unroll 1
+        for (int p = 0; p < 8; ++p) {
+          const int half = p >> 2, part = p & 3;
+          const int jb = 2 * c.J + half;  // 128-column block
+          if (jb < c.I) continue;         // below the diagonal: the mirror of another tile
+          if (jb == c.I && part < e) continue;
+          const bool dblk = jb == c.I && part == e;
+          const int cl0 = half * 128 + part * 32;  // tile-local column of the block
+          const int c0 = c.J * BN + cl0;
+          // direct: rows row0.., columns c0.. (row-major copy); mirror: rows
+          // c0.., columns row0.. (transposed copy)
+          const float* yd = tile + (size_t)(32 * e) * BN + cl0;
+          const float* ym = tile + kTileFloats + (size_t)cl0 * BM + 32 * e;
+          if constexpr (MODE == 1) {
+            const double th = c.ep.st->theta;
+            const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
+            gemm1_pass<BF16, false>(c.ep, yd, BN, row0, c0, dblk, thf, f2th, thtb, pp, dpart);
+            gemm1_pass<BF16, true>(c.ep, ym, BM, c0, row0, dblk, thf, f2th, thtb, pp, dpart);
+          } else if constexpr (MODE == 2) {
+            gemm2_pass<BF16, false>(c.ep, yd, BN, row0, c0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
+            gemm2_pass<BF16, true>(c.ep, ym, BM, c0, row0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
+          } else if constexpr (MODE == 4) {
+            const float inv = (float)(1.0 / (kRefScale * check_delta_scale(c.ep.st->R)));
+            check_seg(c.ep, row0 + lane, c0, jb == c.I, yd + lane * BN, inv, pp, dpart);
+          } else {
+            refine_seg(c.ep, row0 + lane, c0, jb == c.I, yd + lane * BN);
+          }
         }
       }
+      if (has) {
+        __syncwarp();
+        if (lane == 0 && ok) mbar_arrive(&sempty_bar[slot]);
+        ++u;
+      }
       if (MODE == 1 || MODE == 4) {
-        // FP64 arithmetic is slow on this part: only warps on a diagonal
-        // block (warp-uniform) reduce the FP64 sums, and six lanes of warp
-        // 0 add the warps' rows of the table in parallel.  The table is
-        // double-buffered by the count of reduced tiles, so one barrier per
-        // tile suffices: a warp writes this buffer again only after the
-        // next tile's barrier, which warp 0 reaches after reading it.
+        // per-tile partials: element sums in FP32 (a float shuffle tree),
+        // the diagonal sums in FP64 only on tiles that reach the diagonal
+        // (FP64 arithmetic is slow on this part); lanes of warp 12 add the
+        // four warps' rows in a fixed order.  The table is double-buffered
+        // by the count of reduced tiles, so one barrier per tile suffices.
         const float s2 = warp_sum_f(pp[0]), s3 = warp_sum_f(pp[1]), s4 = warp_sum_f(pp[2]);
         double d0 = 0.0, d1 = 0.0;
-        if (jb == c.I) {
+        if (tile_diag) {
           d0 = warp_sum(dpart[0]);
           d1 = warp_sum(dpart[1]);
         }
-        double* r = red + (nred & 1) * 40;
+        double* r = red + (nred & 1) * 20;
         if (lane == 0) {
-          r[dw * 5] = d0;
-          r[dw * 5 + 1] = d1;
-          r[dw * 5 + 2] = (double)s2;
-          r[dw * 5 + 3] = (double)s3;
-          r[dw * 5 + 4] = (double)s4;
+          r[e * 5] = d0;
+          r[e * 5 + 1] = d1;
+          r[e * 5 + 2] = (double)s2;
+          r[e * 5 + 3] = (double)s3;
+          r[e * 5 + 4] = (double)s4;
         }
-        drain_bar_sync();
-        if (dw == 0 && lane < kPartFields) {
-          double sacc = 0.0;
-          if (lane < 5)
-            for (int w = 0; w < 8; ++w) sacc += r[w * 5 + lane];
-          ep.part[(size_t)t * kPartFields + lane] = sacc;
-        }
-        ++nred;
       }
-      if (!ok) break;
+      // one barrier per tile: publishes the table and decides, uniformly,
+      // whether the epilogue warps go on
+      const bool stop = bar_red_or(kEpiBarrier, kEpiThreads, !ok);
+      if ((MODE == 1 || MODE == 4) && e == 0 && lane < kPartFields) {
+        const double* r = red + (nred & 1) * 20;
+        double sacc = 0.0;
+        if (lane < 5)
+          for (int w = 0; w < 4; ++w) sacc += r[w * 5 + lane];
+        ep.part[(size_t)t * kPartFields + lane] = sacc;
+      }
+      ++nred;
+      if (stop) break;
     }
   }
   tc_fence_before();
@@ -843,38 +940,44 @@ int sm_count() {
   return n;
 }
 
+// Launch on at most one CTA per SM (persistent tiles).  `ep.scratch` must
+// hold tc_scratch_bytes(): two tile slots for every CTA of the grid.
 template <int MODE, bool BF16, bool BATCHED>
-int launch_tc(const TcOperands* A, const TcOperands* B, const Epi& ep, const BatchItem* items,
+int launch_tc(const TcOperands* A, const TcOperands* B, Epi ep, const BatchItem* items,
               const int* tile_inst, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<MODE, BF16, BATCHED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes<MODE>());
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return 1;
     // the register split must fit the pool the CTA is launched with, or
     // the drain warpgroups' setmaxnreg.inc would wait forever
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<MODE, BF16, BATCHED>) != cudaSuccess ||
-        fa.numRegs * kThreads < (int)(128 * kCtlRegs + 256 * kDrainRegs))
+        fa.numRegs * kThreads < (int)(128 * kCtlRegs + 256 * kDrainRegs + 128 * kEpiRegs))
       return 1;
     attr = true;
   }
+  if (!ep.scratch) return 1;
+  if (ep.wait_ns == 0) ep.wait_ns = kWaitNs;
   const int grid = ep.ntiles < sm_count() ? ep.ntiles : sm_count();
+  if (grid <= 0) return 0;
   if (BATCHED) {
     CUtensorMap dummy;
     memset(&dummy, 0, sizeof dummy);
-    tc_gemm_kernel<MODE, BF16, true><<<grid, kThreads, smem_bytes<MODE>(), s>>>(
-        dummy, dummy, dummy, dummy, ep, items, tile_inst);
+    tc_gemm_kernel<MODE, BF16, true><<<grid, kThreads, kSmemBytes, s>>>(dummy, dummy, dummy, dummy,
+                                                                     ep, items, tile_inst);
   } else {
-    tc_gemm_kernel<MODE, BF16, false><<<grid, kThreads, smem_bytes<MODE>(), s>>>(A->hi, A->lo, B->hi, B->lo,
-                                                                         ep, nullptr, nullptr);
+    tc_gemm_kernel<MODE, BF16, false><<<grid, kThreads, kSmemBytes, s>>>(A->hi, A->lo, B->hi, B->lo,
+                                                                      ep, nullptr, nullptr);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 }  // namespace
 
 int tc_pad(int M) { return ((M + BN - 1) / BN) * BN; }
+
+size_t tc_scratch_bytes() { return (size_t)sm_count() * 2 * kSlotFloats * sizeof(float); }
 
 int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int errlen, int box_k) {
   return encode_map((CUtensorMap*)map, ptr, Mp, bf16, err, errlen, box_k);
@@ -902,8 +1005,12 @@ void tc_free_operands(TcOperands* op) { delete op; }
 
 int tc_launch_gemm1(const TcOperands* opX, const float* X, float* Sig, void* Sh, void* Sl, int M,
                     int Mp, const void* H, int h_f64, int ldh, double* part, State* st, int bf16,
-                    float split_scale, int* /*dev_err*/, cudaStream_t s) {
+                    float split_scale, float* scratch, cudaStream_t s, unsigned long long wait_ns,
+                    int stall) {
   Epi ep{};
+  ep.scratch = scratch;
+  ep.wait_ns = wait_ns;
+  ep.stall = stall;
   ep.X = X;
   ep.Sig = nullptr;
   ep.out = Sig;
@@ -925,8 +1032,9 @@ int tc_launch_gemm1(const TcOperands* opX, const float* X, float* Sig, void* Sh,
 
 int tc_launch_gemm2(const TcOperands* opS, const TcOperands* opX, const float* X, const float* Sig,
                     float* Xn, void* Xnh, void* Xnl, int M, int Mp, State* st, int bf16,
-                    float split_scale, int* /*dev_err*/, cudaStream_t s) {
+                    float split_scale, float* scratch, cudaStream_t s) {
   Epi ep{};
+  ep.scratch = scratch;
   ep.X = X;
   ep.Sig = Sig;
   ep.out = Xn;
@@ -948,8 +1056,10 @@ void tc_set_smem_attrs() {}
 
 int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const double* S64,
                         const double* D64, double* Dn64, const double* xscale,
-                        const double* dscale, int M, int Mp, State* st, cudaStream_t s) {
+                        const double* dscale, int M, int Mp, State* st, float* scratch,
+                        cudaStream_t s) {
   Epi ep{};
+  ep.scratch = scratch;
   ep.st = st;
   ep.M = M;
   ep.Mp = Mp;
@@ -980,8 +1090,9 @@ int tc_make_device_maps(void** dev, const void* hi, const void* lo, int Mp, char
 
 int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void* emaps,
                     const double* S64, const double* D1, double* part, int M, int Mp, State* st,
-                    cudaStream_t s) {
+                    float* scratch, cudaStream_t s) {
   Epi ep{};
+  ep.scratch = scratch;
   ep.emaps = (const CUtensorMap*)emaps;
   ep.st = st;
   ep.M = M;
@@ -1008,9 +1119,11 @@ int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* er
 }
 
 int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
-                         int ntiles, double* part, int bf16, float split_scale, cudaStream_t s) {
+                         int ntiles, double* part, int bf16, float split_scale, float* scratch,
+                         cudaStream_t s) {
   (void)batch;
   Epi ep{};
+  ep.scratch = scratch;
   ep.part = part;
   ep.ntiles = ntiles;
   ep.split_scale = split_scale;
