@@ -570,8 +570,8 @@ def reverse_mode_grad(H, N, n_iter, G_D=None, g_E=0.0):
         T3 = float(np.sum(S * D))
         den = T1 - T2
         Ds.append(D)
-        if den <= 16.0 * M * U_FP64 * max(1.0, T1):
-            aux.append(None)  # identity step past the 0/0 guard
+        if abs(den) <= 16.0 * M * U_FP64 * max(1.0, T1):
+            aux.append(None)  # identity step past the 0/0 guard (|den|, as in solve)
             continue
         c = (T2 - T3) / den
         aux.append((T1, T2, c))

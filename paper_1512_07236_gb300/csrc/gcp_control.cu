@@ -7,8 +7,10 @@
 //
 // Stop rules (readings where the paper is silent, shared with the oracle):
 //   * ||D^2 - D||_F <= tol or Tr(D - D^2) <= tol (the paper's test);
-//   * 0/0 guard: Tr(D - D^2) <= 16 M u max(1, Tr D) ends the loop
-//     (in fixed-iteration mode the step becomes an identity step);
+//   * 0/0 guard: when |Tr(D - D^2)| <= 16 M u max(1, Tr D) and the stop
+//     test still fails, the FP64 step is a McWeeny step (c = 1/2, the limit
+//     of the recursion as gamma -> 0, Eq. mcweeny3) and the split phase
+//     ends; in fixed-iteration mode the step becomes an identity step;
 //   * c_0 outside [0,1] reports GCP_ERR_ILL_CONDITIONED (Eqs. pmcpcons2-3);
 //   * FP64 stagnation: once R < 1e-8, two consecutive non-decreasing R;
 //   * split-precision floor: once R < 1e-2, a step that fails to reduce R

@@ -14,6 +14,8 @@ import pytest
 
 from paper_1512_07236_gb300 import inputs
 
+from conftest import SUBSPACE_BF16, SUBSPACE_TARGET
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -43,7 +45,9 @@ def _checks(D, N, Ht):
     return R, tr, comm
 
 
-@pytest.mark.parametrize("prec,fro_lim", [("mixed_fp16", 2e-6), ("mixed_bf16", 4e-5)])
+# mixed_fp16 is held to the stated target; mixed_bf16 misses it (see conftest)
+@pytest.mark.parametrize("prec,fro_lim", [("mixed_fp16", SUBSPACE_TARGET),
+                                          ("mixed_bf16", SUBSPACE_BF16)])
 def test_dense_8192_mixed(solver, dense8192, prec, fro_lim):
     M, N, H, eps, Q = dense8192
     Ht = torch.from_numpy(H).cuda()

@@ -13,6 +13,8 @@ import pytest
 from oracle import gcp_oracle as o
 from paper_1512_07236_gb300 import inputs
 
+from conftest import SUBSPACE_BF16, SUBSPACE_TARGET
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -72,8 +74,10 @@ def test_mixed_solve_parity(solver, prec, refine, M, N, gap, seed):
     # the subspace keeps the rotation left by the split phase; its size is
     # set by the representation (2^-22 fp16, 2^-17 bf16) and by the
     # truncating FP32 accumulation of the tensor cores
-    lim = 3e-6 if prec == "mixed_fp16" else 2e-5
-    assert dmax <= lim and dfro <= lim, (dmax, dfro)
+    if prec == "mixed_fp16":
+        assert dfro <= SUBSPACE_TARGET and dmax <= 3 * SUBSPACE_TARGET, (dmax, dfro)
+    else:  # mixed_bf16 misses the target (see conftest)
+        assert dfro <= SUBSPACE_BF16 and dmax <= SUBSPACE_BF16, (dmax, dfro)
     assert abs(info["energy"] - ref["E"]) <= 1e-9 * abs(ref["E"])
     assert info["iters_lowp"] >= 1 and info["iters_fp64"] >= 1
 
@@ -115,7 +119,9 @@ def test_mixed_with_float32_hamiltonian(solver):
     D, info = solver.solve(_dev(H, torch.float32), M // 2, prec="mixed_fp16", tol=1e-10)
     assert info["status"] == 0
     assert abs(info["energy"] - ref["E"]) / M <= 1e-10
-    assert np.abs(D.cpu().numpy() - ref["D"]).max() <= 3e-6
+    Dg = D.cpu().numpy()
+    assert np.linalg.norm(Dg - ref["D"]) / np.sqrt(M // 2) <= SUBSPACE_TARGET
+    assert np.abs(Dg - ref["D"]).max() <= 3 * SUBSPACE_TARGET
 
 
 def test_slice_refinement_agrees_with_fp64_refinement(solver):
