@@ -179,6 +179,15 @@ def oracle_sample(H, N, iters):
     return time.perf_counter() - t0, r["iters"]
 
 
+def dtype_label(prec, M=None, tol=TOL):
+    """The arithmetic a precision option runs: split products (two 16-bit
+    halves, three products) then FP64 refinement for the mixed modes."""
+    if prec == "mixed_auto":  # the library's rule (include/gcp.h)
+        prec = "fp64" if (M is not None and M < 512) or tol < 1e-10 else "mixed_fp16"
+    return {"fp64": "f64", "fp16x3": "fp16x3", "bf16x3": "bf16x3",
+            "mixed_fp16": "fp16x3+f64", "mixed_bf16": "bf16x3+f64"}.get(prec, prec)
+
+
 # The headline metric, shared by both arms.
 METRIC = "GCP effective TFLOP/s (dense-equivalent 4 M^3 per step) to ||D^2-D||_F<=1e-6"
 
@@ -266,7 +275,8 @@ def run_workload(args, rank):
                                          stream)
         line.update({
             "metric": "time to ||D^2-D||_F<=1e-6, tight-binding insulator", "value": ms * 1e-3,
-            "unit": "s", "higher_is_better": False, "ms_per_step": ms, "dtype": "fp16x3+f64",
+            "unit": "s", "higher_is_better": False, "ms_per_step": ms,
+            "dtype": dtype_label(args.prec, M),
             "config": {"workload": "simple-cubic 20^3 tight-binding, t=-1, onsite +-0.5, "
                                    "disorder 0.1, FP32 storage, N=4000", "M": M, "N": N,
                        "prec": args.prec, "guess": args.guess, "iters": info["iters"]},
@@ -297,7 +307,7 @@ def run_workload(args, rank):
         line.update({
             "metric": "batched solves/s to ||D^2-D||_F<=1e-6", "value": 512 / (ms * 1e-3),
             "unit": "solves/s", "higher_is_better": True, "ms_per_step": ms,
-            "dtype": "fp16x3+f64" if "mixed" in args.prec else args.prec,
+            "dtype": dtype_label(args.prec),
             "config": {"workload": "512 rotated spectra, M in {64,96,...,1024}, N=M/4, "
                                    "gap U[0.02,0.2]", "prec": args.prec, "guess": args.guess,
                        "sum_M2": int(sum(H.shape[0] ** 2 for H in Hs))},
@@ -543,7 +553,7 @@ def main():
             "metric": METRIC,
             "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp16x3+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(args.prec, M),
             "data": "synthetic",
             "config": {"workload": workload_name(M, N, args.gap),
                        "M": M, "N": N, "gap": args.gap, "prec": args.prec,

@@ -68,13 +68,24 @@ typedef enum { GCP_F64 = 0, GCP_F32 = 1 } gcp_dtype;
  *   GCP_MIXED_FP16  FP16X3 until the residual stagnates, then refinement
  *                   steps in FP64 arithmetic until the stop test holds
  *                   (gcp_options.refine picks how their products run).
- *   GCP_MIXED_BF16  BF16X3 bulk, the same refinement.                    */
+ *   GCP_MIXED_BF16  BF16X3 bulk, the same refinement.  Its subspace error
+ *                   (about 1e-5 at M = 8192, gap 0.01) is ten times that of
+ *                   GCP_MIXED_FP16: the 8-bit bf16 halves carry 16 bits of X.
+ *   GCP_MIXED_AUTO  picks the arithmetic from the problem: GCP_FP64 when
+ *                   M < 512 (the tensor-core tiles are mostly padding there
+ *                   and the FP64 products are cheap) or tol < 1e-10 (below
+ *                   the floor of the exact-slice refinement at large M),
+ *                   GCP_MIXED_FP16 otherwise.  The gap of H, the other
+ *                   factor in the subspace error of the split phase, is not
+ *                   known before the solve.  gcp_result reports what ran
+ *                   (iters_lowp > 0 for the mixed path).                   */
 typedef enum {
   GCP_FP64 = 0,
   GCP_FP16X3 = 1,
   GCP_BF16X3 = 2,
   GCP_MIXED_FP16 = 3,
-  GCP_MIXED_BF16 = 4
+  GCP_MIXED_BF16 = 4,
+  GCP_MIXED_AUTO = 5
 } gcp_precision;
 
 typedef enum {
@@ -101,6 +112,17 @@ typedef struct {
                           products and HPCP steps (always used otherwise) */
   int guess;           /* gcp_guess (default GCP_GUESS_CANONICAL) */
   int method;          /* gcp_method (default GCP_METHOD_HPCP) */
+  int refine_iters;    /* mixed modes: at most this many refinement steps
+                          (0, the default: only max_iter bounds them); a
+                          solve that hits the cap without meeting tol returns
+                          GCP_ERR_NOT_CONVERGED with the last iterate */
+  int check_symmetry;  /* 1: before solving, measure max_ij |H_ij - H_ji| and
+                          return GCP_ERR_INVALID_ARG when it exceeds
+                          sym_tol * max_ij |H_ij| (default 0: not checked;
+                          the split-precision paths read only the upper
+                          triangle of H, the FP64 path all of it) */
+  double sym_tol;      /* relative bound of the symmetry check (default 0:
+                          exact symmetry) */
 } gcp_options;
 
 /* Initial guess.
@@ -232,12 +254,27 @@ gcp_status gcp_backward(void* handle, const void* H, int M, int N, int ld, int h
  * M <= 512 (larger M returns GCP_ERR_INVALID_ARG with a message in err).
  * The array is shared by every call on a device and keeps the previous
  * call's contents; calls whose GPU work overlaps race on it, so order them.
- * The first call on a device looks up the array's device address (make it
- * before any stream capture).  err (host, may be NULL): errlen bytes for a
- * one-line message.  Synchronous at exit like gcp_solve. */
+ * The first call on a device looks up the array's device address.  The
+ * step loop is driven from the host (a state read and a stream
+ * synchronisation after every step), so the call is synchronous and must not
+ * be made while its stream is being captured into a CUDA graph.
+ * GCP_MIXED_AUTO runs this FP64 path.  A loop that ends without the stop
+ * test returns GCP_ERR_NOT_CONVERGED.  err (host, may be NULL): errlen bytes
+ * for a one-line message. */
 gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int h_dtype, void* D_out,
                              int ldd, int d_dtype, gcp_result* res, const gcp_options* opt,
                              char* err, int errlen);
+
+/* Diagnostic (no counterpart in the paper): exercise the bounded waits of the
+ * tensor-core kernel.  Launches one split-precision GEMM1 of size M on the
+ * workspace of this handle with every device-side wait bounded by wait_s
+ * seconds (0 < wait_s <= 10), after making its drain warps first wait on a
+ * barrier that no thread arrives on: every role of the kernel reaches its
+ * bound, records the timeout and returns (TMEM freed, context usable).
+ * Returns GCP_ERR_TIMEOUT when the kernel reported it, which is the expected
+ * result, GCP_OK if it did not.  The workspace contents are overwritten: a
+ * following gcp_solve on the handle starts afresh. */
+gcp_status gcp_debug_timeout(void* handle, int M, double wait_s, const gcp_options* opt);
 
 /* Diagnostic (no counterpart in the paper): time the two products of one
  * step on the workspace left by the last gcp_solve on this handle (same M;

@@ -441,6 +441,7 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
     Ctl ctl = make_ctl(a, 0, 1);
     const bool oz = use_oz(a);
     ctl.mcw_only = oz ? 1 : 0;
+    ctl.phase_max = mixed ? a.o.refine_iters : 0;
     auto step = [&](int src, cudaGraphConditionalHandle c, cudaStream_t ss) {
       return oz ? rec_oz_step(h, a, src, ctl, c, graph ? 1 : 0, ss)
                 : rec_f64_step(h, a, src, ctl, c, graph ? 1 : 0, ss);
@@ -498,7 +499,34 @@ bool valid_dtype(int d) { return d == GCP_F64 || d == GCP_F32; }
 
 bool valid_modes(const gcp_options& o) {
   return o.guess >= GCP_GUESS_CANONICAL && o.guess <= GCP_GUESS_HOLE &&
-         (o.method == GCP_METHOD_HPCP || o.method == GCP_METHOD_PMCP);
+         (o.method == GCP_METHOD_HPCP || o.method == GCP_METHOD_PMCP) && o.refine_iters >= 0 &&
+         (o.check_symmetry == 0 || o.check_symmetry == 1) && o.sym_tol >= 0.0 &&
+         o.sym_tol <= 1.0;
+}
+
+// GCP_MIXED_AUTO: the FP64 path for small M (the tensor-core tiles would be
+// mostly padding and the FP64 products are cheap) or a tolerance below the
+// exact-slice refinement's floor, the split-FP16 path with refinement
+// otherwise.
+constexpr int kAutoMixedMinM = 512;
+int resolve_prec(int prec, int M, double tol) {
+  if (prec != GCP_MIXED_AUTO) return prec;
+  return (M < kAutoMixedMinM || tol < 1e-10) ? GCP_FP64 : GCP_MIXED_FP16;
+}
+
+// Optional check that H is symmetric (gcp_options.check_symmetry).
+gcp_status check_symmetry(Handle* h, const void* H, int h_f64, int M, int ld, double rel,
+                          cudaStream_t s, const char* who) {
+  gcp_status r = ensure_common(h, 1, M, 0);
+  if (r != GCP_OK) return r;
+  launch_sym_check(H, h_f64, M, ld, h->gpart, s);
+  double v[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(v, h->gpart, sizeof v, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!(v[0] <= rel * v[1]))
+    return fail(h, GCP_ERR_INVALID_ARG, "%s: H is not symmetric: max|H_ij - H_ji| = %.3e > %.3e",
+                who, v[0], rel * v[1]);
+  return GCP_OK;
 }
 
 }  // namespace
@@ -517,6 +545,9 @@ void gcp_default_options(gcp_options* o) {
   o->history_cap = 0;
   o->use_graph = 1;
   o->stream = nullptr;
+  o->refine_iters = 0;
+  o->check_symmetry = 0;
+  o->sym_tol = 0.0;
 }
 
 const char* gcp_status_string(int s) {
@@ -686,10 +717,15 @@ gcp_status gcp_solve(void* hv, const void* H, int M, int N, int ld, int h_dtype,
   else
     gcp_default_options(&o);
   if (!H || !D_out || M <= 0 || N < 0 || N > M || ld < M || ldd < M || !valid_dtype(h_dtype) ||
-      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_AUTO || o.max_iter < 0 ||
       o.history_cap < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || !valid_modes(o))
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve: bad arguments");
+  o.prec = resolve_prec(o.prec, M, o.tol);
   cudaStream_t s = (cudaStream_t)o.stream;
+  if (o.check_symmetry) {
+    gcp_status r = check_symmetry(h, H, h_dtype == GCP_F64, M, ld, o.sym_tol, s, "gcp_solve");
+    if (r != GCP_OK) return r;
+  }
   if (res) memset(res, 0, sizeof *res);
   if (N == 0 || N == M) {
     launch_fill(nullptr, D_out, d_dtype == GCP_F64, M, ldd, N == 0 ? 0.0 : 1.0, s);
@@ -789,14 +825,25 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   else
     gcp_default_options(&o);
   if (batch <= 0 || !H || !M || !N || !ld || !D_out || !valid_dtype(h_dtype) ||
-      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_BF16 || o.max_iter < 0 ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_AUTO || o.max_iter < 0 ||
       !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || o.history_cap != 0)
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad arguments");
   if (!valid_modes(o)) return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad guess or method");
-  for (int b = 0; b < batch; ++b)
+  int maxM_all = 0;
+  for (int b = 0; b < batch; ++b) {
     if (!H[b] || !D_out[b] || M[b] <= 0 || N[b] < 0 || N[b] > M[b] || ld[b] < M[b])
       return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad instance %d", b);
+    if (M[b] > maxM_all) maxM_all = M[b];
+  }
+  // one arithmetic for the whole batch, chosen from its largest instance
+  o.prec = resolve_prec(o.prec, maxM_all, o.tol);
   cudaStream_t s = (cudaStream_t)o.stream;
+  if (o.check_symmetry)
+    for (int b = 0; b < batch; ++b) {
+      gcp_status r = check_symmetry(h, H[b], h_dtype == GCP_F64, M[b], ld[b], o.sym_tol, s,
+                                    "gcp_solve_batched");
+      if (r != GCP_OK) return fail(h, r, "%s (instance %d)", h->err.c_str(), b);
+    }
   const bool split = is_split(o.prec), mixed = is_mixed(o.prec);
   const int bf16 = split_bf16(o.prec);
   const int h64 = h_dtype == GCP_F64, d64 = d_dtype == GCP_F64;
@@ -1017,6 +1064,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   c0.endgame = split ? 1 : 0;
   c0.u = kU64;
   c0.mcw_only = oz ? 1 : 0;
+  c0.phase_max = mixed ? o.refine_iters : 0;
   c1.method = c0.method = o.method;
 
   auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
@@ -1080,8 +1128,11 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       if (e != cudaSuccess) return fail(h, GCP_ERR_CUDA, "body capture: %s", cudaGetErrorString(e));
       return GCP_OK;
     }
-    const int cap = (o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
-    for (int it = 0; it < cap; ++it) {
+    // the control kernel stops every instance by max_iter (fixed_iters)
+    // evaluations; the bound here only guards the host loop (64-bit: no
+    // overflow for any int option)
+    const long long cap = (long long)(o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
+    for (long long it = 0; it < cap; ++it) {
       gcp_status rr = body(0, ss, 0);
       if (rr != GCP_OK) return rr;
       int hostact = 0;
@@ -1182,6 +1233,48 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
                                   o.fixed_iters, o.ckpt_every, h->D64[0], h->D64[1], h->S64,
                                   h->part, h->gpart, h->st, h->hist, s, err, sizeof err);
   if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
+  return GCP_OK;
+}
+
+// Diagnostic: drive the bounded-wait path of the tensor-core kernel.  One
+// split GEMM1 of size M on this handle's workspace (its inputs are whatever
+// the buffers hold: only the waits matter), every device-side wait bounded by
+// wait_s, and the drain warps first wait on a barrier that no thread arrives
+// on.  Every role of the kernel then runs into its bound, records the
+// timeout in the state and returns; the kernel frees its TMEM and leaves the
+// context usable.
+gcp_status gcp_debug_timeout(void* hv, int M, double wait_s, const gcp_options* opt) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  gcp_options o;
+  if (opt)
+    o = *opt;
+  else
+    gcp_default_options(&o);
+  if (M <= 0 || !(wait_s > 0.0) || wait_s > 10.0)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_debug_timeout: bad arguments (0 < wait_s <= 10)");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int Mp = tc_pad(M);
+  gcp_status r;
+  if ((r = ensure_common(h, tc_num_tiles(Mp), M, 0)) != GCP_OK) return r;
+  if ((r = ensure_split(h, Mp, 0)) != GCP_OK) return r;
+  State init;
+  memset(&init, 0, sizeof init);
+  init.theta = 0.25;
+  CK(cudaMemcpyAsync(h->st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+  const unsigned long long ns = (unsigned long long)(wait_s * 1e9);
+  if (tc_launch_gemm1(h->opX[0], h->X[0], h->Sig, h->Sh, h->Sl, M, Mp, nullptr, 1, M, h->part,
+                      h->st, 0, kSplitScale, h->tcs, s, ns, 1))
+    return fail(h, GCP_ERR_CUDA, "gcp_debug_timeout: launch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  State hs;
+  CK(cudaMemcpyAsync(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // leave the state as a fresh solve expects it
+  memset(&init, 0, sizeof init);
+  CK(cudaMemcpyAsync(h->st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "gcp_debug_timeout: the kernel gave up waiting");
   return GCP_OK;
 }
 

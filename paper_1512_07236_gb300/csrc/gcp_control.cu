@@ -143,7 +143,8 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
       // running on to its floor
       stop = 1;
       kind = 2;
-    } else if (n >= ctl.max_iter) {
+    } else if (n >= ctl.max_iter || (ctl.phase_max > 0 && n - st->n_phase0 >= ctl.phase_max)) {
+      // max_iter, or the step cap of this phase (refine_iters)
       stop = 1;
       kind = 3;
       status = GCP_ERR_NOT_CONVERGED;
@@ -401,6 +402,7 @@ __device__ void state_init_dev(State* st, int phase) {
   st->hist_n = 0;
   st->converged = 0;
   st->terminal = 0;
+  st->n_phase0 = 0;
   if (st->no_gap) {  // D = theta I, nothing to iterate
     st->stopped = 1;
     st->terminal = 1;
@@ -420,6 +422,7 @@ __device__ void phase_begin_dev(State* st, int phase) {
   st->stopped = go ? 0 : 1;
   st->phase = phase;
   st->parity = 0;
+  st->n_phase0 = st->n;
   st->Rp0 = st->Rp1 = INFINITY;
 }
 

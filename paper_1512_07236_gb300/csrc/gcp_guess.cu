@@ -222,9 +222,41 @@ __global__ void guess_write_x_kernel(const T* __restrict__ H, int M, int ld, flo
 }
 }  // namespace
 
+// max_{i<j} |H_ij - H_ji| and max_ij |H_ij|: one row i per block.y, the
+// columns j > i of that row against column i below the diagonal; block
+// maxima go to out[] with an integer atomicMax on the bit patterns (for
+// non-negative doubles the order of the bits is the order of the values).
+template <typename T>
+__global__ void sym_check_kernel(const T* __restrict__ H, int M, int ld,
+                                 unsigned long long* __restrict__ out) {
+  const int i = blockIdx.y;
+  double asym = 0.0, amax = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    const double a = (double)H[(size_t)i * ld + j];
+    amax = fmax(amax, fabs(a));
+    if (j > i) asym = fmax(asym, fabs(a - (double)H[(size_t)j * ld + i]));
+  }
+  asym = warp_max(asym);
+  amax = warp_max(amax);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(asym));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(amax));
+  }
+}
+
 int guess_partial_blocks(int M) {
   int b = (M + (kGuessThreads / 32) - 1) / (kGuessThreads / 32);
   return b < kGuessMaxBlocks ? b : kGuessMaxBlocks;
+}
+
+void launch_sym_check(const void* H, int h_f64, int M, int ld, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, 2 * sizeof(double), s);
+  dim3 grid((M + 255) / 256 < 8 ? (M + 255) / 256 : 8, M);
+  if (h_f64)
+    sym_check_kernel<double><<<grid, 256, 0, s>>>((const double*)H, M, ld,
+                                                  (unsigned long long*)out);
+  else
+    sym_check_kernel<float><<<grid, 256, 0, s>>>((const float*)H, M, ld, (unsigned long long*)out);
 }
 
 void launch_guess_reduce(const void* H, int h_f64, int M, int ld, double* part, cudaStream_t s) {

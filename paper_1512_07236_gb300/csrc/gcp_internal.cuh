@@ -25,7 +25,7 @@ struct State {
   int hist_n;
   int converged;    // the stop test held
   int terminal;     // stopped for good (max_iter, stagnation, hard error)
-  int pad_;
+  int n_phase0;     // n when the current phase began
   double c, a, b;           // c_n and the polynomial coefficients of D_{n+1}
   double T1, T2, T3, R, E;  // traces of the last evaluated iterate
   double Rp0, Rp1;          // residuals of the two previous evaluated iterates
@@ -47,6 +47,7 @@ struct Ctl {
   int endgame;      // McWeeny endgame (split and refinement phases only)
   int mcw_only;     // every step is a McWeeny step (exact-slice refinement)
   int method;       // gcp_method
+  int phase_max;    // > 0: at most this many steps in this phase
   double tol;
   double u;         // unit roundoff of the phase's state (den guard)
 };
@@ -112,6 +113,9 @@ void launch_guess_reduce(const void* H, int h_f64, int M, int ld, double* part, 
 // (gcp_guess mode; the HPCP+ search reads the diagonal of H), into State.
 void launch_guess_finalize(const double* part, int nblocks, int M, int N, const void* H,
                            int h_f64, int ld, int guess_mode, State* st, cudaStream_t s);
+// max_{i<j} |H_ij - H_ji| and max_ij |H_ij| into out[0], out[1] (device,
+// zeroed here first).
+void launch_sym_check(const void* H, int h_f64, int M, int ld, double* out, cudaStream_t s);
 // D0 = theta I + beta2 (mu I - H) (FP64 or FP32 out), padded area zero.
 void launch_guess_write_d(const void* H, int h_f64, int M, int ld, void* D, int d_f64, int ldd,
                           int rows_pad, const State* st, cudaStream_t s);

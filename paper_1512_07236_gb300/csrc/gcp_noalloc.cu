@@ -18,10 +18,12 @@
 //     overlaps on the GPU (two host threads, or two streams without ordering)
 //     race on the array and give wrong results: order them.
 //   * The first call on a device looks up the device address of the array
-//     (cudaGetSymbolAddress) with that device current and caches it; make
-//     that first call before any stream capture begins.
-//   * The iteration loop is driven from the host (one small state read per
-//     step); FP64 products only (the arithmetic of gcp_solve with GCP_FP64).
+//     (cudaGetSymbolAddress) with that device current and caches it.
+//   * The iteration loop is driven from the host: every step ends with a
+//     read of the solver state and a stream synchronisation, so the call is
+//     synchronous and must not be made while its stream is being captured.
+//   * FP64 products only (the arithmetic of gcp_solve with GCP_FP64);
+//     GCP_MIXED_AUTO takes that path too.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -106,6 +108,7 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
     set_err(err, errlen, "gcp_solve_noalloc: bad arguments");
     return GCP_ERR_INVALID_ARG;
   }
+  if (o.prec == GCP_MIXED_AUTO) o.prec = GCP_FP64;  // the only arithmetic here
   if (o.prec != GCP_FP64 || o.history_cap != 0) {
     set_err(err, errlen, "gcp_solve_noalloc: only prec = GCP_FP64 without history");
     return GCP_ERR_UNSUPPORTED;
@@ -171,16 +174,24 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
   ctl.u = kU64;
   ctl.method = o.method;
   double* buf[2] = {D0, D1};
-  const int cap = (o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
-  for (int it = 0; it < cap; ++it) {
-    const int src = it & 1;
+  // The control kernel stops the loop by max_iter (or fixed_iters) steps; the
+  // host bound is a guard in 64-bit arithmetic (no overflow for any int
+  // option).  A loop that ends without the control kernel's stop reports
+  // GCP_ERR_NOT_CONVERGED.
+  const long long cap = (long long)(o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) + 2;
+  bool stopped = false;
+  for (long long it = 0; it < cap; ++it) {
+    const int src = (int)(it & 1);
     launch_f64_gemm1(buf[src], S, M, M, nullptr, h64, ld, part, st, s);
     launch_control(part, f64_num_tiles(M), st, nullptr, ctl, 0ull, 0, s);
     launch_f64_gemm2(S, buf[src], buf[src ^ 1], M, M, st, s);
     NA_CK(cudaPeekAtLastError());
     NA_CK(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
-    if (hs.stopped) break;
+    if (hs.stopped) {
+      stopped = true;
+      break;
+    }
   }
   launch_copy_out_f64(D0, D1, st, M, M, D_out, d64, ldd, s);
   launch_energy(D_out, d64, ldd, H, h64, ld, M, gpart, st, s);
@@ -203,6 +214,10 @@ extern "C" gcp_status gcp_solve_noalloc(const void* H, int M, int N, int ld, int
     res->alpha = hs.alpha;
     res->hmin = hs.hmin;
     res->hmax = hs.hmax;
+  }
+  if (!stopped && hs.status == GCP_OK) {
+    hs.status = GCP_ERR_NOT_CONVERGED;
+    if (res) res->status = GCP_ERR_NOT_CONVERGED;
   }
   if (hs.status != GCP_OK)
     set_err(err, errlen, "gcp_solve_noalloc: solve ended: %s", gcp_status_string(hs.status));

@@ -21,21 +21,24 @@ OK, ERR_INVALID_ARG, ERR_NOT_CONVERGED, ERR_ILL_CONDITIONED, ERR_NO_GAP, ERR_NON
 # gcp_dtype
 F64, F32 = 0, 1
 # gcp_precision
-PRECISIONS = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "mixed_fp16": 3, "mixed_bf16": 4}
+PRECISIONS = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "mixed_fp16": 3, "mixed_bf16": 4,
+              "mixed_auto": 5}
 STOPS = {"idem_fro": 0, "trace": 1}
 GUESSES = {"canonical": 0, "hpcp+": 1, "hole": 2}
 METHODS = {"hpcp": 0, "pmcp": 1}
 HISTORY_FIELDS = 8
 EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destroy",
            "gcp_last_error", "gcp_init_guess", "gcp_step", "gcp_solve", "gcp_get_history",
-           "gcp_solve_batched", "gcp_backward", "gcp_time_kernels", "gcp_solve_noalloc")
+           "gcp_solve_batched", "gcp_backward", "gcp_time_kernels", "gcp_solve_noalloc",
+           "gcp_debug_timeout")
 
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("stop", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("fixed_iters", C.c_int), ("ckpt_every", C.c_int),
                 ("history_cap", C.c_int), ("use_graph", C.c_int), ("stream", C.c_void_p),
-                ("refine", C.c_int), ("guess", C.c_int), ("method", C.c_int)]
+                ("refine", C.c_int), ("guess", C.c_int), ("method", C.c_int),
+                ("refine_iters", C.c_int), ("check_symmetry", C.c_int), ("sym_tol", C.c_double)]
 
 
 class Result(C.Structure):
@@ -90,9 +93,10 @@ def load_library(path: str = LIB_PATH):
         lib.gcp_time_kernels.argtypes = [vp, ip, ip, ip, ip, C.POINTER(dp), C.POINTER(Options)]
         lib.gcp_solve_noalloc.argtypes = [vp, ip, ip, ip, ip, vp, ip, ip, C.POINTER(Result),
                                           C.POINTER(Options), C.c_char_p, ip]
+        lib.gcp_debug_timeout.argtypes = [vp, ip, dp, C.POINTER(Options)]
         for name in ("gcp_create", "gcp_destroy", "gcp_init_guess", "gcp_step", "gcp_solve",
                      "gcp_get_history", "gcp_solve_batched", "gcp_backward", "gcp_time_kernels",
-                     "gcp_solve_noalloc"):
+                     "gcp_solve_noalloc", "gcp_debug_timeout"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -117,7 +121,8 @@ def _check_matrix(t: torch.Tensor, name: str):
 
 def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_iters=0,
                  ckpt_every=8, history_cap=0, use_graph=True, stream=None,
-                 refine="slices", guess="canonical", method="hpcp") -> Options:
+                 refine="slices", guess="canonical", method="hpcp", refine_iters=0,
+                 check_symmetry=False, sym_tol=0.0) -> Options:
     lib = load_library()
     o = Options()
     lib.gcp_default_options(C.byref(o))
@@ -132,6 +137,9 @@ def make_options(prec="fp64", stop="idem_fro", tol=1e-12, max_iter=100, fixed_it
     o.refine = {"slices": 0, "fp64": 1}[refine] if isinstance(refine, str) else int(refine)
     o.guess = GUESSES[guess] if isinstance(guess, str) else int(guess)
     o.method = METHODS[method] if isinstance(method, str) else int(method)
+    o.refine_iters = int(refine_iters)
+    o.check_symmetry = 1 if check_symmetry else 0
+    o.sym_tol = float(sym_tol)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -196,9 +204,8 @@ class Solver:
         _check_matrix(H, "H")
         M = H.shape[0]
         if out is None:
-            dt = out_dtype or (torch.float64 if opts.get("prec", "fp64") in ("fp64", 0, "mixed_fp16",
-                                                                            "mixed_bf16", 3, 4)
-                               else torch.float32)
+            dt = out_dtype or (torch.float64 if opts.get("prec", "fp64") in (
+                "fp64", 0, "mixed_fp16", "mixed_bf16", "mixed_auto", 3, 4, 5) else torch.float32)
             out = torch.empty((M, M), dtype=dt, device=H.device)
         _check_matrix(out, "out")
         res = Result()
@@ -223,9 +230,8 @@ class Solver:
             if H.dtype != Hs[0].dtype:
                 raise TypeError("all H must share a dtype")
         if outs is None:
-            dt = out_dtype or (torch.float64 if opts.get("prec", "fp64") in ("fp64", 0, "mixed_fp16",
-                                                                            "mixed_bf16", 3, 4)
-                               else torch.float32)
+            dt = out_dtype or (torch.float64 if opts.get("prec", "fp64") in (
+                "fp64", 0, "mixed_fp16", "mixed_bf16", "mixed_auto", 3, 4, 5) else torch.float32)
             outs = [torch.empty((H.shape[0], H.shape[0]), dtype=dt, device=H.device) for H in Hs]
         for k, D in enumerate(outs):
             _check_matrix(D, f"out[{k}]")
@@ -284,6 +290,13 @@ class Solver:
         if p in (PRECISIONS["mixed_fp16"], PRECISIONS["mixed_bf16"]):
             return ms[0], ms[1], ms[2]
         return ms[0], ms[1]
+
+    def debug_timeout(self, M, wait_s=1e-3):
+        """gcp_debug_timeout: run one split GEMM1 of size M whose waits are
+        bounded by wait_s seconds while its drain warps wait on a barrier
+        nobody arrives on; returns the status (GCP_ERR_TIMEOUT expected)."""
+        o = make_options()
+        return self.lib.gcp_debug_timeout(self.h, int(M), float(wait_s), C.byref(o))
 
     def history(self, cap=1000):
         buf = (C.c_double * (cap * HISTORY_FIELDS))()

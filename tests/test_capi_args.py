@@ -49,7 +49,8 @@ def _solve(lib, h, H=FAKE, M=64, N=16, ld=64, hd=gcp.F64, D=FAKE, ldd=64, dd=gcp
     dict(H=None), dict(D=None), dict(M=0), dict(N=-1), dict(N=65), dict(ld=63), dict(ldd=63),
     dict(hd=7), dict(dd=7), dict(prec=99), dict(prec=-1), dict(max_iter=-1),
     dict(history_cap=-1), dict(tol=math.nan), dict(tol=-1.0), dict(stop=2), dict(guess=3),
-    dict(method=2),
+    dict(method=2), dict(prec=6), dict(refine_iters=-1), dict(check_symmetry=2),
+    dict(sym_tol=-1e-3), dict(sym_tol=math.nan), dict(sym_tol=2.0),
 ])
 def test_solve_rejects(lib, handle, case):
     assert _solve(lib, handle, **case) == gcp.ERR_INVALID_ARG
@@ -109,3 +110,29 @@ def test_backward_rejects(lib, handle, kw, expect):
     o = _opts(**kw)
     assert lib.gcp_backward(handle, FAKE, 64, 16, 64, gcp.F64, None, 1.0, FAKE,
                             C.byref(o)) == expect
+
+
+def test_defaults_of_the_added_options(lib):
+    o = gcp.Options()
+    lib.gcp_default_options(C.byref(o))
+    assert o.refine_iters == 0 and o.check_symmetry == 0 and o.sym_tol == 0.0
+
+
+def test_batched_rejects_added_options(lib, handle):
+    n = 1
+    Hs = (C.c_void_p * n)(FAKE.value)
+    Ds = (C.c_void_p * n)(FAKE.value)
+    Ms, Ns, lds = (C.c_int * n)(64), (C.c_int * n)(16), (C.c_int * n)(64)
+    res = (gcp.Result * n)()
+    for kw in (dict(prec=6), dict(refine_iters=-2), dict(check_symmetry=-1)):
+        o = _opts(**kw)
+        assert lib.gcp_solve_batched(handle, n, Hs, Ms, Ns, lds, gcp.F64, Ds, gcp.F64, res,
+                                     C.byref(o)) == gcp.ERR_INVALID_ARG, kw
+
+
+@pytest.mark.parametrize("M,wait_s", [(0, 1e-3), (-5, 1e-3), (256, 0.0), (256, -1.0),
+                                      (256, 11.0), (256, math.nan)])
+def test_debug_timeout_rejects(lib, handle, M, wait_s):
+    o = gcp.make_options(stream=0)
+    assert lib.gcp_debug_timeout(handle, M, wait_s, C.byref(o)) == gcp.ERR_INVALID_ARG
+    assert lib.gcp_debug_timeout(None, 256, 1e-3, C.byref(o)) == gcp.ERR_INVALID_ARG

@@ -3,16 +3,23 @@ not allocate device memory while solving (a memory pool that already holds
 the GPU, a latency-bound loop that cannot take cudaMalloc's implicit
 synchronisation, code without a library handle).
 
-Calls the entry point directly through the C ABI and compares it with
-gcp_solve (the handle-based path) on two calls in a row, within the FP64
-parity tolerance of the other tests.  Kept in a file that sorts last so a
-run that stops at the first failure has already run every other test; it
-also passes alone in a fresh process."""
+Each case calls the entry point directly through the C ABI and compares it
+with gcp_solve (the handle-based path, bitwise: the same kernels) and with
+the FP64 oracle (the FP64 bar of the other parity tests): the workspace
+maximum M = 512, FP32 input and output, leading dimensions larger than M,
+the trivial fillings N = 0 and N = M, the trace stop, the PMCP recursion,
+fixed_iters and a max_iter far beyond what the solve needs.  Two calls in a
+row (the second smaller than the first) show that the shared array's stale
+contents do not leak, and the device's free memory is unchanged across a
+call.  Kept in a file that sorts last, so a run that stops at the first
+failure has already run every other test; it also passes alone in a fresh
+process."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+from oracle import gcp_oracle as o
 from paper_1512_07236_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -21,48 +28,133 @@ torch = pytest.importorskip("torch")
 
 
 @pytest.fixture(scope="module")
-def lib():
+def g():
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     from paper_1512_07236_gb300 import gcp
     return gcp
 
 
+@pytest.fixture(scope="module")
+def solver(g):
+    return g.Solver()
+
+
 def _noalloc(g, H, N, out, **opts):
     L = g.load_library()
     res = g.Result()
-    o = g.make_options(**opts)
+    opt = g.make_options(**opts)
     err = C.create_string_buffer(256)
     st = L.gcp_solve_noalloc(C.c_void_p(H.data_ptr()), H.shape[0], int(N), H.stride(0),
                              g.F64 if H.dtype == torch.float64 else g.F32,
                              C.c_void_p(out.data_ptr()), out.stride(0),
                              g.F64 if out.dtype == torch.float64 else g.F32, C.byref(res),
-                             C.byref(o), err, 256)
+                             C.byref(opt), err, 256)
     torch.cuda.synchronize()
     return st, res, err.value.decode()
 
 
-def test_noalloc_matches_solve_twice_in_a_row(lib):
-    g = lib
-    solver = g.Solver()
-    cases = [(256, 64, (-1.0, -0.1), (0.1, 1.0), 1), (130, 33, (-1.0, -0.05), (0.05, 1.0), 2)]
-    for M, N, occ, virt, seed in cases:
-        H, eps, Q = inputs.rotated_spectrum(M, N, occ, virt, seed=seed)
-        Ht = torch.from_numpy(H).cuda()
-        Dref, iref = solver.solve(Ht, N, prec="fp64", tol=1e-12)
+def _padded(A, ld, dtype):
+    """A (M x M) inside an M x ld device buffer (leading dimension ld)."""
+    M = A.shape[0]
+    buf = torch.full((M, ld), float("nan"), dtype=dtype, device="cuda")
+    buf[:, :M] = torch.from_numpy(A).to(dtype)
+    return buf[:, :M]
+
+
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+CASES = [
+    # M, N, gap, seed, H dtype, D dtype, ld of H, ld of D, options
+    (256, 64, 0.2, 1, torch.float64, torch.float64, 256, 256, dict()),
+    (130, 33, 0.1, 2, torch.float64, torch.float64, 130, 130, dict()),
+    (512, 128, 0.1, 3, torch.float64, torch.float64, 512, 512, dict()),
+    (200, 50, 0.2, 4, torch.float32, torch.float32, 200, 200, dict()),
+    (200, 50, 0.2, 5, torch.float32, torch.float64, 208, 256, dict()),
+    (160, 40, 0.2, 6, torch.float64, torch.float64, 192, 176, dict(stop="trace", tol=1e-10)),
+    (160, 40, 0.2, 7, torch.float64, torch.float64, 160, 160, dict(method="pmcp")),
+    (96, 24, 0.2, 8, torch.float64, torch.float64, 96, 96, dict(fixed_iters=9)),
+    (64, 16, 0.2, 9, torch.float64, torch.float64, 64, 64, dict(max_iter=2**31 - 1)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"M{c[0]}-{c[4]}-{c[5]}-ld{c[6]}-{c[8]}")
+def test_noalloc_matches_solve_and_oracle(g, solver, case):
+    M, N, gap, seed, hdt, ddt, ldh, ldd, opts = case
+    H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -gap / 2), (gap / 2, 1.0), seed=seed)
+    Hd = _padded(H, ldh, hdt)
+    kw = dict(prec="fp64", tol=1e-12)
+    kw.update(opts)
+    Dn = _padded(np.zeros((M, M)), ldd, ddt)
+    # the first call may load the library's module (lazy loading allocates
+    # its globals); the second call of the pair is measured
+    st0, res0, msg0 = _noalloc(g, Hd, N, Dn, **kw)
+    first = Dn.clone()
+    free0 = _free_bytes()
+    st, res, msg = _noalloc(g, Hd, N, Dn, **kw)
+    assert _free_bytes() == free0  # nothing allocated on the device
+    assert st0 == st and torch.equal(first, Dn) and res0.iters == res.iters
+    Dref, iref = solver.solve(Hd, N, out=_padded(np.zeros((M, M)), ldd, ddt), **kw)
+    assert st == g.OK, msg
+    assert res.status == g.OK and res.iters == iref["iters"]
+    assert torch.equal(Dn, Dref)
+    assert res.energy == iref["energy"]
+    # the oracle on the same input (the FP32 input rounded as the device sees it)
+    Hh = Hd.double().cpu().numpy()
+    okw = {k: v for k, v in kw.items() if k in ("tol", "stop", "fixed_iters", "method",
+                                                    "max_iter")}
+    if "max_iter" in okw:
+        okw["max_iter"] = 100
+    ref = o.solve(Hh, N, **okw)
+    bar = 1e-10 if ddt == torch.float64 else 1e-6
+    assert np.abs(Dn.double().cpu().numpy() - ref["D"]).max() <= bar
+    assert abs(res.energy - ref["E"]) <= 1e-12 * abs(ref["E"]) + (0 if ddt == torch.float64
+                                                                  else 1e-6 * M)
+    assert abs(res.iters - ref["iters"]) <= 1
+
+
+@pytest.mark.parametrize("N", [0, 96])
+def test_noalloc_trivial_fillings(g, N):
+    M = 96
+    H, eps, Q = inputs.rotated_spectrum(M, 24, (-1.0, -0.1), (0.1, 1.0), seed=11)
+    Hd = torch.from_numpy(H).cuda()
+    Dn = torch.full((M, M), float("nan"), dtype=torch.float64, device="cuda")
+    st, res, msg = _noalloc(g, Hd, N, Dn, prec="fp64")
+    assert st == g.OK, msg
+    expect = torch.eye(M, dtype=torch.float64, device="cuda") * (1.0 if N == M else 0.0)
+    assert torch.equal(Dn, expect)
+    assert abs(res.energy - (float(np.trace(H)) if N == M else 0.0)) <= 1e-12 * M
+
+
+def test_noalloc_twice_in_a_row_smaller_second(g, solver):
+    """The shared array keeps the first call's contents; the second, smaller
+    call must not see them."""
+    outs = []
+    for M, N, seed in ((512, 128, 21), (130, 33, 22)):
+        H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.05), (0.05, 1.0), seed=seed)
+        Hd = torch.from_numpy(H).cuda()
         Dn = torch.full((M, M), float("nan"), dtype=torch.float64, device="cuda")
-        st, res, msg = _noalloc(g, Ht, N, Dn, prec="fp64", tol=1e-12)
+        st, res, msg = _noalloc(g, Hd, N, Dn, prec="fp64", tol=1e-12)
+        Dref, iref = solver.solve(Hd, N, prec="fp64", tol=1e-12)
         assert st == g.OK, msg
-        assert res.status == g.OK and res.iters == iref["iters"]
-        assert float((Dn - Dref).abs().max()) <= 1e-12
-        assert abs(res.energy - iref["energy"]) <= 1e-12 * abs(iref["energy"])
-        assert abs(res.trace - N) <= 1e-10
+        assert torch.equal(Dn, Dref) and res.iters == iref["iters"]
+        outs.append(res.iters)
+    assert len(outs) == 2
 
 
-def test_noalloc_rejects_sizes_beyond_its_workspace(lib):
-    g = lib
+def test_noalloc_rejects_sizes_beyond_its_workspace(g):
     H = torch.eye(520, dtype=torch.float64, device="cuda")
     D = torch.empty_like(H)
     st, res, msg = _noalloc(g, H, 100, D, prec="fp64")
     assert st == g.ERR_INVALID_ARG
     assert "exceeds" in msg and "512" in msg
+
+
+def test_noalloc_rejects_other_precisions(g):
+    H = torch.eye(64, dtype=torch.float64, device="cuda")
+    D = torch.empty_like(H)
+    st, res, msg = _noalloc(g, H, 16, D, prec="mixed_fp16")
+    assert st == g.ERR_UNSUPPORTED and "GCP_FP64" in msg
