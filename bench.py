@@ -289,7 +289,8 @@ def run_workload(args, rank):
         items = inputs.batched_rotated(512, qr_backend="torch")
         Hs = [torch.from_numpy(H).cuda() for H, _, _, _ in items]
         Ns = [N for _, N, _, _ in items]
-        opts = dict(prec=args.prec, tol=TOL, guess=args.guess, method=args.method)
+        opts = dict(prec=args.prec, tol=TOL, guess=args.guess, method=args.method,
+                    use_graph=not args.no_graph)
         for _ in range(W):
             solver.solve_batched(Hs, Ns, **opts)
         with ClockSampler(0) as clk:
