@@ -78,14 +78,27 @@ typedef enum { GCP_F64 = 0, GCP_F32 = 1 } gcp_dtype;
  *                   GCP_MIXED_FP16 otherwise.  The gap of H, the other
  *                   factor in the subspace error of the split phase, is not
  *                   known before the solve.  gcp_result reports what ran
- *                   (iters_lowp > 0 for the mixed path).                   */
+ *                   (iters_lowp > 0 for the mixed path).
+ *   GCP_FP32        an FP32 state with split-FP16 tensor-core products: for
+ *                   gcp_solve the arithmetic of GCP_FP16X3; for
+ *                   gcp_backward the tensor-core adjoint (forward, segment
+ *                   recomputation and the adjoint's three products per step
+ *                   on the tensor cores, FP32 elementwise work).
+ *                   Fixed-iteration split solves (the recursion
+ *                   gcp_backward differentiates) take c_n as a free-running
+ *                   split solve does: Eq. mcwgamb with the rounding drift of
+ *                   Tr D absorbed (Tr D_{n+1} = N), the McWeeny step once
+ *                   ||D^2 - D||_F < 0.05; where a free-running solve would
+ *                   stop at the floor of its products, the remaining steps
+ *                   are identity steps.                                     */
 typedef enum {
   GCP_FP64 = 0,
   GCP_FP16X3 = 1,
   GCP_BF16X3 = 2,
   GCP_MIXED_FP16 = 3,
   GCP_MIXED_BF16 = 4,
-  GCP_MIXED_AUTO = 5
+  GCP_MIXED_AUTO = 5,
+  GCP_FP32 = 6
 } gcp_precision;
 
 typedef enum {
@@ -99,7 +112,9 @@ typedef struct {
   double tol;          /* stop tolerance (default 1e-12) */
   int max_iter;        /* cap on steps (default 100) */
   int fixed_iters;     /* > 0: run exactly this many steps, no stop test;
-                          steps past the 0/0 guard become identity steps */
+                          steps past the 0/0 guard (split precisions: or
+                          past the floor of the products) become identity
+                          steps */
   int ckpt_every;      /* checkpoint interval for gcp_backward (default 8) */
   int history_cap;     /* > 0: record up to this many per-step records */
   int use_graph;       /* 1 (default): device-side loop in one CUDA graph;
@@ -233,8 +248,12 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
 /* Reverse-mode derivative of L = <G_D, D_K> + g_E * Tr(H D_K), where D_K is
  * the iterate after exactly opt->fixed_iters steps of Eq. hpcp3 from the
  * guess of H (Eq. dmguess, Eq. pmcpguess); c_n depends on D_n (Eq. mcwgamb)
- * and the adjoint includes that dependence.  FP64 (opt->prec = GCP_FP64).
- * H: device M x M (ld, h_dtype); G_D: device M x M (ld, h_dtype) or NULL;
+ * and the adjoint includes that dependence.  opt->prec: GCP_FP64 (FP64
+ * iterates and products) or GCP_FP32 (the iterates of a GCP_FP32
+ * fixed-iteration solve, products on the tensor cores; the derivative of
+ * that computed recursion).
+ * H: device M x M (ld, h_dtype); G_D: device M x M (ld, h_dtype) or NULL
+ * (D_K is symmetric, so only the symmetric part of G_D matters);
  * dL_dH: device M x M (ld, h_dtype), written, symmetric (the derivative with
  * respect to a symmetric H; the Gershgorin bound contributes a subgradient).
  * Runs the forward pass itself, keeping a checkpoint every opt->ckpt_every

@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgcp.so")
 
 SOURCES = ["gcp_guess.cu", "gcp_fp64.cu", "gcp_control.cu", "gcp_tc.cu", "gcp_capi.cu",
-           "gcp_noalloc.cu", "gcp_adjoint.cu", "gcp_ozaki.cu"]
+           "gcp_noalloc.cu", "gcp_adjoint.cu", "gcp_adjoint_tc.cu", "gcp_ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -284,7 +284,53 @@ struct AdjWs {
   size_t bytes = 0;
 };
 
+double* g_guess_tmp = nullptr;  // per-process scratch of adjoint_guess (device)
+
 }  // namespace
+
+// dL/dH from G0 = dL/dD_0 (FP64, M x M): the guess adjoint of Eq. dmguess /
+// Eq. pmcpguess (see the header comment) plus g_E D_K.
+int adjoint_guess(const void* H, int M, int N, int ld, int h_f64, const double* G0,
+                  const double* DK, double gE, void* dLdH, double* gpart, State* st,
+                  cudaStream_t s, char* err, int errlen) {
+#define AG_CK(call)                                                                  \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      snprintf(err, errlen, "gcp_backward: %s: %s", #call, cudaGetErrorString(e_));  \
+      return GCP_ERR_CUDA;                                                           \
+    }                                                                                \
+  } while (0)
+  if (!g_guess_tmp) AG_CK(cudaMalloc((void**)&g_guess_tmp, (3 * kRedBlocks + 64) * sizeof(double)));
+  double* rpart = g_guess_tmp;
+  double* sc = g_guess_tmp + 3 * kRedBlocks;
+  // restore the guess parameters (a replay state may have overwritten them)
+  launch_guess_reduce(H, h_f64, M, ld, gpart, s);
+  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld,
+                        GCP_GUESS_CANONICAL, st, s);
+  if (h_f64) {
+    adj_gersh_kernel<double><<<kRedBlocks, 256, 0, s>>>((const double*)H, ld, M, rpart);
+    adj_gersh_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc);
+    adj_reduce_kernel<double><<<kRedBlocks, 256, 0, s>>>(nullptr, nullptr, nullptr, G0,
+                                                        (const double*)H, ld, M, rpart);
+  } else {
+    adj_gersh_kernel<float><<<kRedBlocks, 256, 0, s>>>((const float*)H, ld, M, rpart);
+    adj_gersh_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc);
+    adj_reduce_kernel<float><<<kRedBlocks, 256, 0, s>>>(nullptr, nullptr, nullptr, G0,
+                                                       (const float*)H, ld, M, rpart);
+  }
+  adj_reduce_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc + 2);
+  if (h_f64)
+    adj_guess_kernel<double><<<row_grid(M), 256, 0, s>>>(G0, (const double*)H, ld, M, st, sc, DK,
+                                                        gE, (double*)dLdH);
+  else
+    adj_guess_kernel<float><<<row_grid(M), 256, 0, s>>>(G0, (const float*)H, ld, M, st, sc, DK, gE,
+                                                       (float*)dLdH);
+  AG_CK(cudaPeekAtLastError());
+  AG_CK(cudaStreamSynchronize(s));
+#undef AG_CK
+  return GCP_OK;
+}
 
 void adjoint_free(void* ws) {
   AdjWs* w = (AdjWs*)ws;
@@ -456,30 +502,7 @@ int adjoint_backward(void** wsp, const void* H, int M, int N, int ld, int h_f64,
     }
   }
   // ---------------- guess ------------------------------------------------
-  // restore the guess parameters (the replay state overwrote the state)
-  launch_guess_reduce(H, h_f64, M, ld, gpart, s);
-  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld,
-                        GCP_GUESS_CANONICAL, st, s);
-  if (h_f64) {
-    adj_gersh_kernel<double><<<kRedBlocks, 256, 0, s>>>((const double*)H, ld, M, rpart);
-    adj_gersh_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc);
-    adj_reduce_kernel<double><<<kRedBlocks, 256, 0, s>>>(nullptr, nullptr, nullptr, G,
-                                                        (const double*)H, ld, M, rpart);
-  } else {
-    adj_gersh_kernel<float><<<kRedBlocks, 256, 0, s>>>((const float*)H, ld, M, rpart);
-    adj_gersh_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc);
-    adj_reduce_kernel<float><<<kRedBlocks, 256, 0, s>>>(nullptr, nullptr, nullptr, G,
-                                                       (const float*)H, ld, M, rpart);
-  }
-  adj_reduce_finalize_kernel<<<1, 32, 0, s>>>(rpart, kRedBlocks, sc + 2);
-  if (h_f64)
-    adj_guess_kernel<double><<<row_grid(M), 256, 0, s>>>(G, (const double*)H, ld, M, st, sc, DK,
-                                                        gE, (double*)dLdH);
-  else
-    adj_guess_kernel<float><<<row_grid(M), 256, 0, s>>>(G, (const float*)H, ld, M, st, sc, DK, gE,
-                                                       (float*)dLdH);
-  AD_CK(cudaPeekAtLastError());
-  AD_CK(cudaStreamSynchronize(s));
+  return adjoint_guess(H, M, N, ld, h_f64, G, DK, gE, dLdH, gpart, st, s, err, errlen);
 #undef AD_CK
   return GCP_OK;
 }

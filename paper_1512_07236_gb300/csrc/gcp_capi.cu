@@ -67,8 +67,10 @@ struct Handle {
   std::vector<char> bkey;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bexec = nullptr;
-  // adjoint workspace (checkpoints, segment iterates, adjoint buffers)
+  // adjoint workspaces (checkpoints, segment iterates, adjoint buffers):
+  // FP64 and FP32 (tensor-core) forms
   void* adj = nullptr;
+  void* adj_tc = nullptr;
   // exact-slice refinement: nine digit slices of D, row scales, BF16 halves
   // of D and of X = D^2 - D with their tensor maps
   int oz_mp = 0;
@@ -510,6 +512,7 @@ bool valid_modes(const gcp_options& o) {
 // otherwise.
 constexpr int kAutoMixedMinM = 512;
 int resolve_prec(int prec, int M, double tol) {
+  if (prec == GCP_FP32) return GCP_FP16X3;  // the same arithmetic for a solve
   if (prec != GCP_MIXED_AUTO) return prec;
   return (M < kAutoMixedMinM || tol < 1e-10) ? GCP_FP64 : GCP_MIXED_FP16;
 }
@@ -581,6 +584,7 @@ gcp_status gcp_destroy(void* hv) {
   cudaFree(h->arena);
   cudaFree(h->tcs);
   adjoint_free(h->adj);
+  adjoint_tc_free(h->adj_tc);
   free_oz(h);
   for (int i = 0; i < 2; ++i) {
     cudaFree(h->D64[i]);
@@ -717,7 +721,7 @@ gcp_status gcp_solve(void* hv, const void* H, int M, int N, int ld, int h_dtype,
   else
     gcp_default_options(&o);
   if (!H || !D_out || M <= 0 || N < 0 || N > M || ld < M || ldd < M || !valid_dtype(h_dtype) ||
-      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_AUTO || o.max_iter < 0 ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_FP32 || o.max_iter < 0 ||
       o.history_cap < 0 || !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || !valid_modes(o))
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve: bad arguments");
   o.prec = resolve_prec(o.prec, M, o.tol);
@@ -825,7 +829,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   else
     gcp_default_options(&o);
   if (batch <= 0 || !H || !M || !N || !ld || !D_out || !valid_dtype(h_dtype) ||
-      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_MIXED_AUTO || o.max_iter < 0 ||
+      !valid_dtype(d_dtype) || o.prec < 0 || o.prec > GCP_FP32 || o.max_iter < 0 ||
       !(o.tol >= 0.0) || (o.stop != 0 && o.stop != 1) || o.history_cap != 0)
     return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad arguments");
   if (!valid_modes(o)) return fail(h, GCP_ERR_INVALID_ARG, "gcp_solve_batched: bad guess or method");
@@ -1219,13 +1223,28 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
       o.fixed_iters <= 0 || o.ckpt_every < 0 || !(g_E == g_E))
     return fail(h, GCP_ERR_INVALID_ARG,
                 "gcp_backward: bad arguments (needs 0 < N < M and opt->fixed_iters > 0)");
-  if (o.prec != GCP_FP64)
-    return fail(h, GCP_ERR_UNSUPPORTED, "gcp_backward: the adjoint runs in FP64 (prec = GCP_FP64)");
+  if (o.prec != GCP_FP64 && o.prec != GCP_FP32)
+    return fail(h, GCP_ERR_UNSUPPORTED,
+                "gcp_backward: the adjoint runs in FP64 or FP32 (prec = GCP_FP64 or GCP_FP32)");
   if (o.guess != GCP_GUESS_CANONICAL || o.method != GCP_METHOD_HPCP)
     return fail(h, GCP_ERR_UNSUPPORTED,
                 "gcp_backward: differentiates the canonical guess and HPCP steps only");
   cudaStream_t s = (cudaStream_t)o.stream;
   gcp_status r;
+  if (o.prec == GCP_FP32) {
+    // iterates in the split state, products on the tensor cores
+    const int Mp = tc_pad(M);
+    size_t nt = tc_num_tiles(Mp);
+    if ((size_t)f64_num_tiles(M) > nt) nt = f64_num_tiles(M);
+    if ((r = ensure_common(h, nt, M, o.fixed_iters + 2)) != GCP_OK) return r;
+    if ((r = ensure_tcs(h)) != GCP_OK) return r;
+    char err[256] = {0};
+    const int rc = adjoint_backward_tc(&h->adj_tc, H, M, N, ld, h_dtype == GCP_F64, G_D, g_E,
+                                       dL_dH, o.fixed_iters, o.ckpt_every, h->st, h->part,
+                                       h->gpart, h->hist, h->tcs, s, err, sizeof err);
+    if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
+    return GCP_OK;
+  }
   if ((r = ensure_common(h, f64_num_tiles(M), M, o.fixed_iters + 2)) != GCP_OK) return r;
   if ((r = ensure_f64(h, M)) != GCP_OK) return r;
   char err[256] = {0};

@@ -159,9 +159,27 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
   // trace it also removes the rounding drift of Tr D (the eigenvalues go to
   // exactly 0 or 1).  The same switch applies while that drift is not small
   // against Tr(D - D^2).  The plain FP64 path keeps the oracle's rule.
-  const bool mcw = ctl.mcw_only || ctl.endgame && ctl.fixed_iters == 0 &&
+  //
+  // Fixed-iteration split phase (the recursion gcp_backward differentiates
+  // in FP32): the same c_n rules, and where a free-running solve would stop
+  // at the floor of its products (the stall rule above), every remaining
+  // step is an identity step.  Without the trace-restoring c and the
+  // endgame, the truncating FP32 accumulation of the tensor cores lets
+  // Tr D drift by ~M 1e-7 per step, c_n leaves [0, 1] once Tr(D - D^2) is
+  // of that size, and the iterate stalls far above the floor.
+  const bool fixed_split = ctl.phase == 1 && ctl.fixed_iters > 0;
+  const bool mcw = ctl.mcw_only || ctl.endgame && (ctl.fixed_iters == 0 || fixed_split) &&
                    (R < 0.05 || fabs(T1 - (double)ctl.N) > 0.05 * fabs(den));
-  if (!stop) {
+  int* kind_out = (ctl.step_kind && fixed_split && n < ctl.fixed_iters) ? ctl.step_kind + n
+                                                                         : nullptr;
+  if (kind_out) *kind_out = kStepIdentity;
+  if (!stop && fixed_split &&
+      (st->split_floor || (ctl.endgame && R < 1e-2 && R > 0.25 * st->Rp0))) {
+    st->split_floor = 1;
+    st->apply = 0;  // identity step
+    st->n = n + 1;
+    st->parity ^= 1;
+  } else if (!stop) {
     // 0/0 guard.  FP64: 16 M u max(1, Tr D) (as in the oracle).  Split phase:
     // the noise of den is set by the FP32 rounding of the O(1) diagonal,
     // 16 sqrt(M) u_32.
@@ -180,7 +198,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
     }
     if (fabs(den) <= den_min && !mcw) {
       if (ctl.fixed_iters > 0) {
-        st->apply = 0;  // identity step
+        st->apply = 0;  // identity step (kind_out already says so)
         st->n = n + 1;
         st->parity ^= 1;
       } else if (R <= ctl.tol) {
@@ -226,7 +244,8 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
         stop = 1;
         kind = 3;
         status = GCP_ERR_ILL_CONDITIONED;
-      } else if (ctl.endgame && n > 0 && !(c >= -0.05 && c <= 1.05) && ctl.fixed_iters == 0) {
+      } else if (ctl.endgame && n > 0 && !(c >= -0.05 && c <= 1.05) &&
+                 (ctl.fixed_iters == 0 || fixed_split)) {
         // c left the stable domain (rounding noise): McWeeny step instead
         set_coeffs(st, 0.5, GCP_METHOD_HPCP);
         st->apply = 1;
@@ -236,6 +255,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
         if (ctl.phase == 1) st->n_lowp += 1;
         st->parity ^= 1;
         if (rec) rec[5] = 0.5;
+        if (kind_out) *kind_out = kStepMcWeeny;
       } else {
         set_coeffs(st, c, method);
         st->apply = 1;
@@ -245,6 +265,7 @@ __device__ int control_decide(const double (&v)[5], State* st, double* hist, con
         if (ctl.phase == 1) st->n_lowp += 1;
         st->parity ^= 1;
         if (rec) rec[5] = c;
+        if (kind_out) *kind_out = mcw ? kStepMcWeeny : kStepRestoring;
       }
     }
   }
@@ -403,6 +424,7 @@ __device__ void state_init_dev(State* st, int phase) {
   st->converged = 0;
   st->terminal = 0;
   st->n_phase0 = 0;
+  st->split_floor = 0;
   if (st->no_gap) {  // D = theta I, nothing to iterate
     st->stopped = 1;
     st->terminal = 1;

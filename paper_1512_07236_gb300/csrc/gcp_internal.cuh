@@ -26,6 +26,8 @@ struct State {
   int converged;    // the stop test held
   int terminal;     // stopped for good (max_iter, stagnation, hard error)
   int n_phase0;     // n when the current phase began
+  int split_floor;  // fixed-iteration split phase: the products stalled,
+                    // every further step is an identity step
   double c, a, b;           // c_n and the polynomial coefficients of D_{n+1}
   double T1, T2, T3, R, E;  // traces of the last evaluated iterate
   double Rp0, Rp1;          // residuals of the two previous evaluated iterates
@@ -50,7 +52,15 @@ struct Ctl {
   int phase_max;    // > 0: at most this many steps in this phase
   double tol;
   double u;         // unit roundoff of the phase's state (den guard)
+  // fixed-iteration split phase: per step, how c_n was taken (kStep*), for
+  // the adjoint; may be null
+  int* step_kind;
 };
+
+// How a step of the fixed-iteration split phase took c_n.
+constexpr int kStepIdentity = 0;   // no update (0/0 guard or stalled products)
+constexpr int kStepRestoring = 1;  // Eq. hpcp3, c_n = (num + (Tr D - N)/2) / den
+constexpr int kStepMcWeeny = 2;    // Eq. hpcp3 with c_n = 1/2 (Eq. mcweeny3)
 
 // Number of partial-sum fields written per GEMM1 tile.
 constexpr int kPartFields = 6;  // T1, T2, T3, R^2, E, spare
@@ -207,6 +217,13 @@ int tc_launch_mcweeny64(const TcOperands* opX, const TcOperands* opD, const doub
 int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void* emaps,
                     const double* S64, const double* D1, double* part, int M, int Mp, State* st,
                     float* scratch, cudaStream_t s);
+// Plain product C = inv_scale (A B) of two split-fp16 operands (Mp x Mp;
+// the kernel computes A B^T, so B is given as the rows of B^T), FP32 out:
+// over all tiles, or (symmetric != 0: the result is known to be symmetric)
+// the upper tiles with the lower triangle mirrored.  st: a state with
+// stopped = 0 (its timeout flag records a wait that gave up).
+int tc_launch_product(const TcOperands* A, const TcOperands* B, float* C, int Mp, int symmetric,
+                      float inv_scale, State* st, float* scratch, cudaStream_t s);
 // Device copies (cudaMalloc'ed, freed with cudaFree) of the hi/lo tensor
 // maps of a pair of Mp x Mp fp16 arrays, for operands named through memory.
 int tc_make_device_maps(void** dev, const void* hi, const void* lo, int Mp, char* err,
@@ -255,6 +272,19 @@ int adjoint_backward(void** ws, const void* H, int M, int N, int ld, int h_f64, 
                      double* S64, double* part, double* gpart, State* st, double* hist,
                      cudaStream_t s, char* err, int errlen);
 void adjoint_free(void* ws);
+// The guess part of the adjoint: dL/dH from G0 = dL/dD_0 and D_K (FP64,
+// M x M), written to dLdH (ld, h dtype).
+int adjoint_guess(const void* H, int M, int N, int ld, int h_f64, const double* G0,
+                  const double* DK, double gE, void* dLdH, double* gpart, State* st,
+                  cudaStream_t s, char* err, int errlen);
+// The same derivative with the iterates in the split state and the
+// products on the tensor cores (FP32; gcp_adjoint_tc.cu).  scratch:
+// tc_scratch_bytes() for the tensor-core kernels; hist: >= K + 2 records.
+int adjoint_backward_tc(void** ws, const void* H, int M, int N, int ld, int h_f64,
+                        const void* GD, double gE, void* dLdH, int K, int ck, State* st,
+                        double* part, double* gpart, double* hist, float* scratch,
+                        cudaStream_t s, char* err, int errlen);
+void adjoint_tc_free(void* ws);
 
 // ---- batched solves (many instances per launch) --------------------------
 // guess: per-instance Gershgorin/trace partials (gstride slots of 4 doubles

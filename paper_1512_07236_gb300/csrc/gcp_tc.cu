@@ -2,7 +2,9 @@
 // TMEM + TMA), with the step's elementwise work fused into the epilogues:
 // mode 1 GEMM1, mode 2 GEMM2 of the split phase; mode 3 the product of an
 // exact-slice refinement step, mode 4 the stop-test product after it
-// (W = D1^2 - D^2 over a K = 3M concatenation of operands).
+// (W = D1^2 - D^2 over a K = 3M concatenation of operands); modes 5 and 6
+// plain products C = A B (FP32 out) for the adjoint, over all tiles (mode 5,
+// a non-symmetric result) or the upper tiles mirrored (mode 6).
 //
 // State.  The iterate is held shifted, X = D - theta J (J = identity on the
 // unpadded M x M block), in FP32, plus two 16-bit halves of s X (s = 2^14):
@@ -182,6 +184,17 @@ __device__ __forceinline__ void load_row32(const float* __restrict__ src, float 
     a[4 * k + 2] = v.z;
     a[4 * k + 3] = v.w;
   }
+}
+
+// All tiles (mode 5, a non-symmetric product), in the same super-column
+// order: t -> (I, J) with I in [0, NI), J in [0, NJ).
+__device__ __forceinline__ void tc_tile_full(int t, int NI, int NJ, int& I, int& J) {
+  const int per = NI * kGroupJ;  // tiles of one full super-column
+  const int j0 = (t / per) * kGroupJ;
+  const int w = (NJ - j0) < kGroupJ ? (NJ - j0) : kGroupJ;
+  const int r = t - (t / per) * per;
+  I = r / w;
+  J = j0 + r % w;
 }
 
 // Refinement-product epilogue of one thread: its row, 32 columns c_base..,
@@ -407,6 +420,41 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
   }
 }
 
+// Plain-product epilogue (modes 5 and 6) of one warp for one 32 x 32 block:
+// C = inv_s2 (A B) in FP32, laid out as gemm1_pass.  Mode 6 writes a block
+// above the diagonal twice (direct and mirror pass).
+template <bool MIRROR>
+__device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restrict__ yb, int ys,
+                                           int orow0, int ocol0, bool diag_blk) {
+  const int lane = threadIdx.x & 31;
+  const int rs = lane >> 3, cl = 4 * (lane & 7);
+  const float sc = ep.inv_s2;
+#pragma unroll
+  for (int jh = 0; jh < 8; jh += 4) {
+    float4 yy[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      yy[j] = __ldcg(reinterpret_cast<const float4*>(yb + (rs + 4 * (jh + j)) * ys + cl));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = orow0 + rs + 4 * (jh + j);
+      const size_t off = (size_t)r * ep.Mp + ocol0 + cl;
+      const float4 o = make_float4(yy[j].x * sc, yy[j].y * sc, yy[j].z * sc, yy[j].w * sc);
+      if (!diag_blk) {
+        *reinterpret_cast<float4*>(ep.out + off) = o;
+      } else {
+        const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = ocol0 + cl + i;
+          if (MIRROR ? (c >= r) : (c < r)) continue;
+          ep.out[off + i] = ov[i];
+        }
+      }
+    }
+  }
+}
+
 // Everything one tile needs: its block coordinates, operand maps, the
 // epilogue pointers of its instance and the update coefficients.
 struct TileCtx {
@@ -425,7 +473,10 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
                                          const int* tile_inst, TileCtx& c) {
   c.ep = base;
   if (!BATCHED) {
-    tc_tile(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
+    if (MODE == 5)
+      tc_tile_full(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
+    else
+      tc_tile(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
     c.skip = false;
     c.ah = mAh;
     c.al = mAl;
@@ -478,7 +529,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
     tc_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
   }
   const State* st = c.ep.st;
-  c.mma = !c.skip && (MODE == 1 || st->apply != 0);
+  c.mma = !c.skip && (MODE == 1 || MODE >= 5 || st->apply != 0);
   c.nkb = c.mma ? (MODE == 4 ? 3 : 1) * (c.ep.Mp / BK) : 0;
   c.ca = c.cb = c.cj = c.cz = 0.f;
   if (MODE == 2 && !c.skip) {
@@ -495,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                    const Epi ep, const BatchItem* items, const int* tile_inst) {
-  if (!BATCHED) {
+  if (!BATCHED && MODE < 5) {
     State* st = ep.st;
     if (st->stopped || st->timeout) return;
   }
@@ -809,9 +860,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int p = 0; p < 8; ++p) {
           const int half = p >> 2, part = p & 3;
           const int jb = 2 * c.J + half;  // 128-column block
-          if (jb < c.I) continue;         // below the diagonal: the mirror of another tile
-          if (jb == c.I && part < e) continue;
-          const bool dblk = jb == c.I && part == e;
+          // below the diagonal: the mirror of another tile (all tiles are
+          // computed in mode 5, a non-symmetric product)
+          if (MODE != 5 && jb < c.I) continue;
+          if (MODE != 5 && jb == c.I && part < e) continue;
+          const bool dblk = MODE != 5 && jb == c.I && part == e;
           const int cl0 = half * 128 + part * 32;  // tile-local column of the block
           const int c0 = c.J * BN + cl0;
           // direct: rows row0.., columns c0.. (row-major copy); mirror: rows
@@ -826,6 +879,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else if constexpr (MODE == 2) {
             gemm2_pass<BF16, false>(c.ep, yd, BN, row0, c0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
             gemm2_pass<BF16, true>(c.ep, ym, BM, c0, row0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
+          } else if constexpr (MODE == 5) {
+            plain_pass<false>(c.ep, yd, BN, row0, c0, false);
+          } else if constexpr (MODE == 6) {
+            plain_pass<false>(c.ep, yd, BN, row0, c0, dblk);
+            plain_pass<true>(c.ep, ym, BM, c0, row0, dblk);
           } else if constexpr (MODE == 4) {
             const float inv = (float)(1.0 / (kRefScale * check_delta_scale(c.ep.st->R)));
             check_seg(c.ep, row0 + lane, c0, jb == c.I, yd + lane * BN, inv, pp, dpart);
@@ -1105,6 +1163,24 @@ int tc_launch_check(const TcOperands* opD, const TcOperands* opDelta, const void
   ep.D64 = D1;
   ep.ld64 = M;
   return launch_tc<4, false, false>(opD, opDelta, ep, nullptr, nullptr, s);
+}
+
+int tc_launch_product(const TcOperands* A, const TcOperands* B, float* C, int Mp, int symmetric,
+                      float inv_scale, State* st, float* scratch, cudaStream_t s) {
+  Epi ep{};
+  ep.scratch = scratch;
+  ep.st = st;
+  ep.M = Mp;
+  ep.Mp = Mp;
+  ep.out = C;
+  ep.split_scale = 1.0f;
+  ep.inv_s2 = inv_scale;
+  if (symmetric) {
+    ep.ntiles = tc_num_tiles(Mp);
+    return launch_tc<6, false, false>(A, B, ep, nullptr, nullptr, s);
+  }
+  ep.ntiles = (Mp / BM) * (Mp / BN);
+  return launch_tc<5, false, false>(A, B, ep, nullptr, nullptr, s);
 }
 
 size_t tc_map_bytes() { return 6 * sizeof(CUtensorMap); }

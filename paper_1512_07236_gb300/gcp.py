@@ -22,7 +22,7 @@ OK, ERR_INVALID_ARG, ERR_NOT_CONVERGED, ERR_ILL_CONDITIONED, ERR_NO_GAP, ERR_NON
 F64, F32 = 0, 1
 # gcp_precision
 PRECISIONS = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "mixed_fp16": 3, "mixed_bf16": 4,
-              "mixed_auto": 5}
+              "mixed_auto": 5, "fp32": 6}
 STOPS = {"idem_fro": 0, "trace": 1}
 GUESSES = {"canonical": 0, "hpcp+": 1, "hole": 2}
 METHODS = {"hpcp": 0, "pmcp": 1}
@@ -254,9 +254,12 @@ class Solver:
             infos.append(d)
         return outs, infos
 
-    def backward(self, H, N, fixed_iters, G_D=None, g_E=0.0, ckpt_every=8, out=None):
+    def backward(self, H, N, fixed_iters, G_D=None, g_E=0.0, ckpt_every=8, out=None,
+                 prec="fp64"):
         """dL/dH of L = <G_D, D_K> + g_E Tr(H D_K), D_K after exactly
-        `fixed_iters` FP64 steps from the guess (gcp_backward)."""
+        `fixed_iters` steps from the guess (gcp_backward).  prec "fp64": the
+        FP64 recursion and adjoint; "fp32": the split-FP16 tensor-core
+        recursion (the iterates of prec="fp32" solves) and its adjoint."""
         _check_matrix(H, "H")
         if G_D is not None:
             _check_matrix(G_D, "G_D")
@@ -267,7 +270,7 @@ class Solver:
         _check_matrix(out, "out")
         if out.dtype != H.dtype or out.stride(0) != H.stride(0):
             raise ValueError("out must match H's dtype and layout")
-        o = make_options(prec="fp64", fixed_iters=fixed_iters, ckpt_every=ckpt_every)
+        o = make_options(prec=prec, fixed_iters=fixed_iters, ckpt_every=ckpt_every)
         st = self.lib.gcp_backward(self.h, C.c_void_p(H.data_ptr()), H.shape[0], int(N),
                                    H.stride(0), _dtype_code(H),
                                    C.c_void_p(G_D.data_ptr() if G_D is not None else 0),

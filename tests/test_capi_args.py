@@ -49,7 +49,7 @@ def _solve(lib, h, H=FAKE, M=64, N=16, ld=64, hd=gcp.F64, D=FAKE, ldd=64, dd=gcp
     dict(H=None), dict(D=None), dict(M=0), dict(N=-1), dict(N=65), dict(ld=63), dict(ldd=63),
     dict(hd=7), dict(dd=7), dict(prec=99), dict(prec=-1), dict(max_iter=-1),
     dict(history_cap=-1), dict(tol=math.nan), dict(tol=-1.0), dict(stop=2), dict(guess=3),
-    dict(method=2), dict(prec=6), dict(refine_iters=-1), dict(check_symmetry=2),
+    dict(method=2), dict(prec=7), dict(refine_iters=-1), dict(check_symmetry=2),
     dict(sym_tol=-1e-3), dict(sym_tol=math.nan), dict(sym_tol=2.0),
 ])
 def test_solve_rejects(lib, handle, case):
@@ -103,6 +103,7 @@ def test_batched_rejects(lib, handle):
 @pytest.mark.parametrize("kw,expect", [
     (dict(fixed_iters=0), gcp.ERR_INVALID_ARG),
     (dict(fixed_iters=5, prec=gcp.PRECISIONS["mixed_fp16"]), gcp.ERR_UNSUPPORTED),
+    (dict(fixed_iters=5, prec=gcp.PRECISIONS["fp16x3"]), gcp.ERR_UNSUPPORTED),
     (dict(fixed_iters=5, guess=gcp.GUESSES["hpcp+"]), gcp.ERR_UNSUPPORTED),
     (dict(fixed_iters=5, method=gcp.METHODS["pmcp"]), gcp.ERR_UNSUPPORTED),
 ])
@@ -124,7 +125,7 @@ def test_batched_rejects_added_options(lib, handle):
     Ds = (C.c_void_p * n)(FAKE.value)
     Ms, Ns, lds = (C.c_int * n)(64), (C.c_int * n)(16), (C.c_int * n)(64)
     res = (gcp.Result * n)()
-    for kw in (dict(prec=6), dict(refine_iters=-2), dict(check_symmetry=-1)):
+    for kw in (dict(prec=7), dict(refine_iters=-2), dict(check_symmetry=-1)):
         o = _opts(**kw)
         assert lib.gcp_solve_batched(handle, n, Hs, Ms, Ns, lds, gcp.F64, Ds, gcp.F64, res,
                                      C.byref(o)) == gcp.ERR_INVALID_ARG, kw

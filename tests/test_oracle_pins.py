@@ -358,3 +358,15 @@ def test_daleckii_krein_matches_fd_of_exact_projector_and_reverse_mode():
         assert float(np.sum(g_dk * E)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
     g_rm, _ = o.reverse_mode_grad(H, N, 40, G_D=V, g_E=1.0)
     np.testing.assert_allclose(g_rm, g_dk, atol=1e-8)
+
+
+@pytest.mark.parametrize("K", [3, 12, 40])
+def test_gradient_of_the_conserved_trace_vanishes(K):
+    """Every step of Eq. hpcp3 with c_n from Eq. mcwgamb keeps Tr D = N, and
+    the guess has Tr D_0 = N for every H: L = Tr D_K is constant, so dL/dH = 0.
+    A dropped or mis-signed dc_n/dD term, or a guess adjoint that loses the
+    trace constraint, leaves an O(1) gradient here."""
+    M, N = 18, 5
+    H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.2), (0.2, 1.0), seed=51)
+    gH, _ = o.reverse_mode_grad(H, N, K, G_D=np.eye(M), g_E=0.0)
+    assert np.abs(gH).max() <= 1e-11
