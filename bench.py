@@ -471,15 +471,15 @@ def main():
                 "achieved_tflops": 2 * alg / ((t1 + t2) * 1e-3) / 1e12,
                 "executed_tflops": 2 * 3 * tile_flops / ((t1 + t2) * 1e-3) / 1e12}
         if "mixed" in args.prec and l64 > 0:
-            o1, o2, o3 = solver.time_kernels(M, N, prec=args.prec, reps=3)
+            o1, o2, o3, npair = solver.time_kernels(M, N, prec=args.prec, reps=3, tol=TOL)
             # each refinement step: slice GEMM, refinement product, stop-test
             # product (the last step's stop test accepts D1 without a further
             # slice GEMM)
             kern["oz_gemm_kernel"] = {
-                "what": "exact digit-slice D^2 of one refinement step", "ms": o1,
-                "launches_per_solve": l64, "ms_per_solve": o1 * l64,
+                "what": f"digit-slice D^2 of one refinement step ({npair} digit-pair products)",
+                "ms": o1, "launches_per_solve": l64, "ms_per_solve": o1 * l64,
                 "achieved_tflops": alg / (o1 * 1e-3) / 1e12,
-                "executed_tflops": (44 if M <= 16384 else 54) * tile_flops / (o1 * 1e-3) / 1e12}
+                "executed_tflops": npair * tile_flops / (o1 * 1e-3) / 1e12}
             kern["tc_gemm_kernel<3>"] = {
                 "what": "refinement product (D^2 - D) D", "ms": o2, "launches_per_solve": l64,
                 "ms_per_solve": o2 * l64, "executed_tflops": 3 * tile_flops / (o2 * 1e-3) / 1e12}

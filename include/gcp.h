@@ -302,10 +302,13 @@ gcp_status gcp_debug_timeout(void* handle, int M, double wait_s, const gcp_optio
  * or GCP_MIXED_BF16 the products of an exact-slice refinement step -- the
  * digit-slice D^2, the fp16 split (D^2 - D) D and the stop-test product
  * W = D1^2 - D^2 -- and needs a prior mixed solve that used that
- * refinement).  Each kernel is launched `reps` times on opt->stream,
- * bracketed by CUDA events; ms (host; 2 doubles, 3 for GCP_MIXED_*)
- * receives the mean duration of each product in milliseconds.  The workspace iterate is overwritten: solve again before
- * reading results. */
+ * refinement; the slice product keeps the digit pairs a solve with
+ * opt->tol keeps).  Each kernel is launched `reps` times on opt->stream,
+ * bracketed by CUDA events; ms (host; 2 doubles, 4 for GCP_MIXED_*)
+ * receives the mean duration of each product in milliseconds, and for
+ * GCP_MIXED_* ms[3] the number of digit-pair products of the slice product.
+ * The workspace iterate is overwritten: solve again before reading
+ * results. */
 gcp_status gcp_time_kernels(void* handle, int M, int N, int prec, int reps, double* ms,
                             const gcp_options* opt);
 

@@ -315,7 +315,7 @@ gcp_status rec_oz_step(Handle* h, const SolveArgs& a, int src, Ctl ctl,
                        cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
   const int M = a.M, Mp = h->oz_mp;
   launch_oz_slice(h->D64[src], M, Mp, h->oz_slices, h->oz_rscale, h->oz_dh, h->oz_dl, h->st, s);
-  if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, Mp, h->st, s))
+  if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, Mp, oz_weight_cap(M, a.o.tol), h->st, s))
     return fail(h, GCP_ERR_CUDA, "slice GEMM launch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   launch_oz_finalize(h->S64, h->D64[src], M, Mp, h->part, h->oz_xh, h->oz_xl, h->oz_xscale,
@@ -443,6 +443,8 @@ gcp_status record_solve(Handle* h, const SolveArgs& a, cudaStream_t s, bool grap
     Ctl ctl = make_ctl(a, 0, 1);
     const bool oz = use_oz(a);
     ctl.mcw_only = oz ? 1 : 0;
+    // the slice product's dropped digit pairs (see oz_weight_cap)
+    if (oz && ctl.stop == GCP_STOP_IDEMP_FRO) ctl.tol -= oz_tail_estimate(M, a.o.tol);
     ctl.phase_max = mixed ? a.o.refine_iters : 0;
     auto step = [&](int src, cudaGraphConditionalHandle c, cudaStream_t ss) {
       return oz ? rec_oz_step(h, a, src, ctl, c, graph ? 1 : 0, ss)
@@ -1069,6 +1071,9 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   c0.u = kU64;
   c0.mcw_only = oz ? 1 : 0;
   c0.phase_max = mixed ? o.refine_iters : 0;
+  // the slice product's dropped digit pairs (the plan of the largest
+  // instance, which every instance shares; see oz_weight_cap)
+  if (oz && c0.stop == GCP_STOP_IDEMP_FRO) c0.tol -= oz_tail_estimate(maxM, o.tol);
   c1.method = c0.method = o.method;
 
   auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
@@ -1092,7 +1097,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   // exact-slice refinement step, as rec_oz_step of a single solve
   auto oz_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
     launch_batch_oz_slice(items_d, nb, maxM, ss);
-    if (launch_batch_oz_gemm(items_d, tinst_tc, ntc, maxM, ss))
+    if (launch_batch_oz_gemm(items_d, tinst_tc, ntc, maxM, oz_weight_cap(maxM, o.tol), ss))
       return fail(h, GCP_ERR_CUDA, "batched slice GEMM launch failed");
     launch_batch_oz_finalize(items_d, nb, maxM, part, ss);
     launch_batch_control(part, items_d, nb, c0, ss);
@@ -1340,7 +1345,8 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   CK(cudaEventRecord(e[0], s));
   for (int r = 0; r < reps; ++r) {
     if (refine) {
-      if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, h->oz_mp, h->st, s))
+      if (launch_oz_gemm(h->oz_op, h->oz_rscale, h->S64, M, h->oz_mp, oz_weight_cap(M, o.tol),
+                         h->st, s))
         return fail(h, GCP_ERR_CUDA, "slice GEMM launch failed");
     } else if (split) {
       if (tc_launch_gemm1(h->opX[0], h->X[0], h->Sig, h->Sh, h->Sl, M, Mp, nullptr, 1, M, h->part,
@@ -1384,7 +1390,10 @@ gcp_status gcp_time_kernels(void* hv, int M, int N, int prec, int reps, double* 
   for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
   ms[0] = t1 / reps;
   ms[1] = t2 / reps;
-  if (refine) ms[2] = t3 / reps;
+  if (refine) {
+    ms[2] = t3 / reps;
+    ms[3] = (double)oz_num_products(M, oz_weight_cap(M, o.tol));
+  }
   State hs;
   CK(cudaMemcpy(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost));
   if (hs.timeout) return fail(h, GCP_ERR_TIMEOUT, "a device-side wait gave up");

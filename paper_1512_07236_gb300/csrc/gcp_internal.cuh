@@ -238,9 +238,16 @@ int oz_make_operands(OzOperands** op, void* const* slices, int Mp, char* err, in
 void oz_free_operands(OzOperands* op);
 void launch_oz_slice(const double* D, int M, int Mp, void* const* slices, double* rscale,
                      void* Dh, void* Dl, const State* st, cudaStream_t s);
-// S = D D exactly up to the slicing (FP64 out, M x M, both triangles).
+// S = D D up to the slicing (FP64 out, M x M, both triangles): digit-pair
+// weights up to wcap (<= 0: all), see oz_weight_cap.
 int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int M, int Mp,
-                   State* st, cudaStream_t s);
+                   int wcap, State* st, cudaStream_t s);
+// Highest digit-pair weight a refinement with stop tolerance tol needs, the
+// estimate of what the dropped weights add to ||D^2 - D||_F (0 with all
+// weights), and the number of digit-pair products of a plan.
+int oz_weight_cap(int M, double tol);
+double oz_tail_estimate(int M, double tol);
+int oz_num_products(int M, int wcap);
 // Partials (Tr D, Tr S, sum S o D, ||S - D||^2, 0) per block for the control
 // kernel, and the fp16 halves of xscale_i X_ij, X = S - D, with a power of
 // two xscale_i per row (max_j |xscale_i X_ij| < 2^13).
@@ -250,7 +257,7 @@ int oz_finalize_blocks(int M);
 void launch_check_halves(const double* D64, const double* D1, int M, int Mp, void* Dh, void* Dl,
                          void* Xh, void* Xl, void* Eh, void* El, const State* st,
                          cudaStream_t s);
-void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
+void launch_oz_finalize(double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s);
 // Digit bits b and slice count of the slicing for an M-long inner dimension.
 int oz_digit_bits(int M);
@@ -259,7 +266,7 @@ int oz_num_slices(int M);
 // tiles), reading and writing the current iterate D64[State::parity].
 void launch_batch_oz_slice(const BatchItem* items, int batch, int maxM, cudaStream_t s);
 int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntiles, int maxM,
-                         cudaStream_t s);
+                         int wcap, cudaStream_t s);
 void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
                               cudaStream_t s);
 size_t oz_batch_map_bytes();

@@ -30,6 +30,7 @@
 // step into one of two TMEM buffers (one buffer per pass, so the MMAs of the
 // next pass overlap the drain of this one), warps 2-9 drain each pass into
 // the FP64 output.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -188,29 +189,48 @@ __global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* it
 // 24 bits to spare in FP32, which holds the residual ||X||_F^2 (per lane,
 // then FP64 across lanes), the row maximum and the halves; a thread keeps
 // its first kFinCache values of the row in registers between the passes.
+// The diagonal of S is replaced by sum_k D_ik^2 formed here in FP64 (a dot
+// product of the row with itself, fixed reduction order), so that Tr S and
+// the diagonal of X do not depend on which digit pairs the slice product
+// kept (its dropped squares are all positive on the diagonal).
 constexpr int kFinThreads = 256;
 constexpr int kFinCache = 32;
 // Block `blk` of `nblk`: rows blk, blk + nblk, ...; partials into part[0..5].
-__device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
+__device__ __forceinline__ void finalize_rows(double* __restrict__ S,
                                               const double* __restrict__ D, int M, int Mp,
                                               int blk, int nblk, double* __restrict__ part,
                                               __half* __restrict__ Xh, __half* __restrict__ Xl,
                                               double* __restrict__ xscale) {
   __shared__ double red[32 * 5];
   __shared__ float mred[32];
+  __shared__ double dred[kFinThreads / 32];
   double v0 = 0.0, v1 = 0.0, v2 = 0.0;  // Tr D, Tr S, sum S o D
   float v3 = 0.f;                       // ||S - D||_F^2
   for (int i = blk; i < Mp; i += nblk) {
     float xc[kFinCache];
     float mx = 0.f;
+    double sii = 0.0;  // (D^2)_ii in FP64
+    if (i < M) {  // uniform over the block
+      double a = 0.0;
+      for (int j = threadIdx.x; j < M; j += kFinThreads) {
+        const double d = D[(size_t)i * M + j];
+        a = fma(d, d, a);
+      }
+      a = warp_sum(a);
+      if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = a;
+      __syncthreads();
+      for (int w = 0; w < kFinThreads / 32; ++w) sii += dred[w];
+      __syncthreads();  // dred is reused by the next row
+    }
 #pragma unroll
     for (int k = 0; k < kFinCache; ++k) {
       const int j = threadIdx.x + k * kFinThreads;
       xc[k] = 0.f;
       if (i < M && j < M) {
         const size_t o = (size_t)i * M + j;
-        const double sv = S[o], dv = D[o];
+        const double sv = i == j ? sii : S[o], dv = D[o];
         if (i == j) {
+          S[o] = sii;
           v0 += dv;
           v1 += sv;
         }
@@ -224,8 +244,9 @@ __device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
     if (i < M)
       for (int j = threadIdx.x + kFinCache * kFinThreads; j < M; j += kFinThreads) {
         const size_t o = (size_t)i * M + j;
-        const double sv = S[o], dv = D[o];
+        const double sv = i == j ? sii : S[o], dv = D[o];
         if (i == j) {
+          S[o] = sii;
           v0 += dv;
           v1 += sv;
         }
@@ -259,7 +280,7 @@ __device__ __forceinline__ void finalize_rows(const double* __restrict__ S,
       float x = 0.f;
       if (i < M && j < M) {
         const size_t o = (size_t)i * M + j;
-        x = (float)(S[o] - D[o]);
+        x = (float)((i == j ? sii : S[o]) - D[o]);
       }
       put(j, x);
     }
@@ -307,7 +328,7 @@ __global__ void __launch_bounds__(256) check_halves_kernel(
 }
 
 __global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
-    const double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
+    double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
     double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
     double* __restrict__ xscale, const State* __restrict__ st) {
   if (st->stopped) return;
@@ -612,13 +633,56 @@ void launch_oz_slice(const double* D, int M, int Mp, void* const* slices, double
 int oz_digit_bits(int M) { return M <= 16384 ? 6 : 5; }
 int oz_num_slices(int M) { return oz_digit_bits(M) == 6 ? 8 : 9; }
 
+// Highest weight a refinement step with stop tolerance tol keeps.  Dropping
+// the weights above W leaves, per element of D^2, the sum over k of the
+// pair terms of weight W + 1: with row scales 2^e <= 1 (|D_ij| <= 1/2 for a
+// near-idempotent D), digits of mean square (B/2)^2 / 3 and independent
+// signs, its size is ~ (B/2)^2/3 B^-(W+3) sqrt(M n_{W+1}) (n_w pairs of
+// weight w), and over the M^2 elements
+//   F(W) = (B/2)^2 / 3  B^-(W+3)  M^1.5  sqrt(n_{W+1})
+// in the Frobenius norm, which adds to ||D^2 - D||_F after the step (the
+// residuals measured against a host FP64 recomputation at M = 257..2048
+// stayed 2-20x below it).  F is taken at the largest M of the digit base
+// (16384 for b = 6, 32768 for b = 5), so that W depends on tol alone and a
+// batch shares the plan of its single solves; W is the smallest weight with
+// F(W) <= tol / 8: tol = 1e-6 gives W = 6 (29 products instead of 44;
+// F = 1.1e-7), tol = 1e-7 W = 7 (37), tol <= 1e-8 all weights.  The diagonal of D^2, whose dropped squares do
+// not cancel, is formed exactly in FP64 whatever W (finalize_rows), so
+// Tr D^2 does not depend on it; the idempotency stop test compares the
+// residual with tol - F(W) (oz_tail_estimate), so that the residual of the
+// exact square of the returned D stays below tol.
+namespace {
+double oz_tail(int db, int W) {
+  const int nsl = db == 6 ? 8 : 9;
+  const double B = (double)(1 << db), h = B / 2.0, Mref = db == 6 ? 16384.0 : 32768.0;
+  const int lo = (W + 1) - (nsl - 1) > 0 ? (W + 1) - (nsl - 1) : 0;
+  const int hi = W + 1 < nsl - 1 ? W + 1 : nsl - 1;
+  const double np = hi >= lo ? (double)(hi - lo + 1) : 0.0;
+  return h * h / 3.0 * pow(B, -(double)(W + 3)) * pow(Mref, 1.5) * sqrt(np);
+}
+}  // namespace
+
+int oz_weight_cap(int M, double tol) {
+  const int db = oz_digit_bits(M), nsl = oz_num_slices(M);
+  for (int W = 2; W < nsl; ++W)
+    if (oz_tail(db, W) <= tol / 8.0) return W;
+  return nsl;
+}
+
+double oz_tail_estimate(int M, double tol) {
+  const int db = oz_digit_bits(M), W = oz_weight_cap(M, tol);
+  if (W >= oz_num_slices(M)) return 0.0;  // all weights: the plan's floor is ~1e-14 M
+  return oz_tail(db, W);
+}
+
 namespace {
 // Passes for an M-long inner dimension: pairs (s, w - s) with
-// 0 <= s, w - s < ns for the kept weights (b = 6: 0..7; b = 5: 0..9), at
-// most floor(2^24 / ((B/2)^2 M)) pairs a pass, then the first dropped square.
-int oz_plan(int M, OzPlan* plan) {
+// 0 <= s, w - s < ns for the kept weights w <= wcap (at most b = 6: 0..8;
+// b = 5: 0..9), at most floor(2^24 / ((B/2)^2 M)) pairs a pass, then the
+// first dropped square.
+int oz_plan(int M, int wcap, OzPlan* plan) {
   const int db = oz_digit_bits(M), nsl = oz_num_slices(M);
-  const int wmax = nsl;  // 8 (b = 6) or 9 (b = 5)
+  const int wmax = (wcap > 0 && wcap < nsl) ? wcap : nsl;  // 8 (b = 6) or 9 (b = 5) at most
   const long long half = 1ll << (db - 1);
   const long long cap = (1ll << 24) / (half * half * M);
   if (cap < 1) return 1;
@@ -637,8 +701,10 @@ int oz_plan(int M, OzPlan* plan) {
       lo += n;
     }
   }
-  // the first dropped square, (5, 5) of weight 10 (see the top of the file)
+  // the first dropped square ((5, 5) of weight 10 for all weights; see the
+  // top of the file)
   const int wsq = (wmax + 1) % 2 == 0 ? wmax + 1 : wmax + 2;
+  if (wsq / 2 >= nsl) return 0;
   if (plan->npass >= kOzMaxPass) return 1;
   plan->w[plan->npass] = wsq;
   plan->s0[plan->npass] = wsq / 2;
@@ -648,8 +714,16 @@ int oz_plan(int M, OzPlan* plan) {
 }
 }  // namespace
 
+int oz_num_products(int M, int wcap) {
+  OzPlan plan;
+  if (oz_plan(M, wcap, &plan)) return 0;
+  int n = 0;
+  for (int p = 0; p < plan.npass; ++p) n += plan.ns[p];
+  return n;
+}
+
 int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int M, int Mp,
-                   State* st, cudaStream_t s) {
+                   int wcap, State* st, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -660,14 +734,14 @@ int launch_oz_gemm(const OzOperands* op, const double* rscale, double* S64, int 
   const int ntiles = tc_num_tiles(Mp);
   const int grid = ntiles < sm_count() ? ntiles : sm_count();
   OzPlan plan;
-  if (oz_plan(M, &plan)) return 1;
+  if (oz_plan(M, wcap, &plan)) return 1;
   oz_gemm_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(op->maps, plan, rscale, S64, M, Mp,
                                                            ntiles, st, nullptr, nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 1;
 }
 
 int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntiles, int maxM,
-                         cudaStream_t s) {
+                         int wcap, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -679,7 +753,7 @@ int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntile
   // the pass plan of the largest instance is valid for every smaller one
   // (and equal to theirs up to M = 7281, where every weight fits one pass)
   OzPlan plan;
-  if (oz_plan(maxM, &plan)) return 1;
+  if (oz_plan(maxM, wcap, &plan)) return 1;
   OzMaps none;
   memset(&none, 0, sizeof none);
   oz_gemm_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(none, plan, nullptr, nullptr, 0, 0,
@@ -723,7 +797,7 @@ void launch_check_halves(const double* D64, const double* D1, int M, int Mp, voi
                                            (__half*)Xl, (__half*)Eh, (__half*)El, st);
 }
 
-void launch_oz_finalize(const double* S64, const double* D64, int M, int Mp, double* part,
+void launch_oz_finalize(double* S64, const double* D64, int M, int Mp, double* part,
                         void* Xh, void* Xl, double* xscale, const State* st, cudaStream_t s) {
   oz_finalize_kernel<<<oz_finalize_blocks(M), kFinThreads, 0, s>>>(
       S64, D64, M, Mp, part, (__half*)Xh, (__half*)Xl, xscale, st);

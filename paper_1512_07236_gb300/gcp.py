@@ -278,20 +278,22 @@ class Solver:
         self._check(st)
         return out
 
-    def time_kernels(self, M, N, prec="fp16x3", reps=10):
+    def time_kernels(self, M, N, prec="fp16x3", reps=10, tol=1e-12):
         """Mean duration (ms) of the two products of one step, CUDA events on
         the current stream; needs a prior solve of size M on this handle.
         prec "fp16x3"/"bf16x3": GEMM1 and GEMM2 of a split step; "fp64": the
         FP64 products; "mixed_fp16"/"mixed_bf16": the digit-slice D^2, the
         (D^2 - D) D product and the stop-test product of an exact-slice
-        refinement step (three values)."""
-        ms = (C.c_double * 3)()
+        refinement step and the number of digit-pair products of the slice
+        product (four values); tol selects those pairs as a solve with that
+        tolerance does."""
+        ms = (C.c_double * 4)()
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-        o = make_options()
+        o = make_options(tol=tol)
         self._check(self.lib.gcp_time_kernels(self.h, int(M), int(N), p, int(reps), ms,
                                               C.byref(o)))
         if p in (PRECISIONS["mixed_fp16"], PRECISIONS["mixed_bf16"]):
-            return ms[0], ms[1], ms[2]
+            return ms[0], ms[1], ms[2], int(ms[3])
         return ms[0], ms[1]
 
     def debug_timeout(self, M, wait_s=1e-3):
