@@ -922,7 +922,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       off += al(oz_batch_map_bytes()) + (kOzSlices + 4) * al(n2 * 2) +
              2 * al((size_t)it.Mp * 8);
       it.oz_off = noz;
-      noz += it.M < 1024 ? it.M : 1024;
+      noz += oz_finalize_blocks(it.M);
     }
   }
   const int nslots = ntc > nf64 ? (ntc > noz ? ntc : noz) : (nf64 > noz ? nf64 : noz);
@@ -1103,6 +1103,14 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
     launch_batch_control(part, items_d, nb, c0, ss);
     if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched refinement product launch failed");
+    if (c0.stop == GCP_STOP_IDEMP_FRO) {
+      // stop test of each new iterate from the split product of K = 3M
+      // (as a single solve), instead of a further slice product
+      launch_batch_check_halves(items_d, nb, maxM, ss);
+      if (tc_launch_batch_gemm(4, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, h->tcs, ss))
+        return fail(h, GCP_ERR_CUDA, "batched stop-test product launch failed");
+      launch_batch_check_control(part, items_d, nb, c0, ss);
+    }
     launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
     CK(cudaPeekAtLastError());
     return GCP_OK;

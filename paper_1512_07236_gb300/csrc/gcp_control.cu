@@ -313,19 +313,7 @@ __global__ void __launch_bounds__(kCtlThreads) control_kernel(const double* __re
 // Otherwise nothing changes and the next step evaluates D1 with the exact
 // product (and stops there if the two disagree about tol).  The WHILE
 // condition is set after this kernel as after the step's control kernel.
-__global__ void __launch_bounds__(kCtlThreads) check_control_kernel(
-    const double* __restrict__ part, int ntiles, State* st, double* hist, Ctl ctl,
-    cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double red[32 * 5];
-  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (!st->stopped)
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-      const double* p = part + (size_t)t * kPartFields;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] += p[k];
-    }
-  block_sum<5>(v, red);
-  if (threadIdx.x != 0) return;
+__device__ void check_decide(const double (&v)[5], State* st, double* hist, const Ctl& ctl) {
   if (!st->stopped && !st->timeout) {
     const double T1 = v[0], T2 = v[1], R = sqrt(fmax(v[3], 0.0));
     if (isfinite(T1) && isfinite(T2) && isfinite(R) && R <= ctl.tol) {
@@ -351,7 +339,46 @@ __global__ void __launch_bounds__(kCtlThreads) check_control_kernel(
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kCtlThreads) check_control_kernel(
+    const double* __restrict__ part, int ntiles, State* st, double* hist, Ctl ctl,
+    cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double red[32 * 5];
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (!st->stopped)
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+      const double* p = part + (size_t)t * kPartFields;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += p[k];
+    }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  check_decide(v, st, hist, ctl);
   if (use_cond) cudaGraphSetConditional(cond, st->stopped ? 0u : 1u);
+}
+
+// Batched stop test after a refinement step: block b sums instance b's
+// tensor-core tile partials in the order of a single solve's
+// check_control_kernel and takes the same decision.
+__global__ void __launch_bounds__(kCtlThreads) batch_check_control_kernel(
+    const double* __restrict__ part, const BatchItem* items, Ctl ctl) {
+  __shared__ double red[32 * 5];
+  const BatchItem& it = items[blockIdx.x];
+  State* st = it.st;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (!st->stopped)
+    for (int t = threadIdx.x; t < it.tc_n; t += blockDim.x) {
+      const double* p = part + (size_t)(it.tc_off + t) * kPartFields;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += p[k];
+    }
+  block_sum<5>(v, red);
+  if (threadIdx.x != 0) return;
+  Ctl c = ctl;
+  c.M = it.M;
+  c.N = it.N;
+  check_decide(v, st, nullptr, c);
 }
 
 // Batched control: block b decides for instance b from its own tiles'
@@ -364,7 +391,7 @@ __global__ void __launch_bounds__(kCtlThreads) batch_control_kernel(const double
   // partial-sum slots: the tensor-core tiles (split phase), the FP64 tiles,
   // or the exact-slice finalize blocks (refinement with mcw_only)
   const int off = ctl.phase == 1 ? it.tc_off : (ctl.mcw_only ? it.oz_off : it.f64_off);
-  const int n = ctl.phase == 1 ? it.tc_n : (ctl.mcw_only ? (it.M < 1024 ? it.M : 1024) : it.f64_n);
+  const int n = ctl.phase == 1 ? it.tc_n : (ctl.mcw_only ? oz_finalize_blocks(it.M) : it.f64_n);
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const double* p = part + (size_t)(off + t) * kPartFields;
@@ -664,40 +691,45 @@ void launch_energy(const void* D, int d_f64, int ldd, const void* H, int h_f64, 
   energy_finalize_kernel<<<1, 32, 0, s>>>(part, nb, st);
 }
 
-// ---- batched elementwise kernels (grid.z / grid.y = instance) ------------
+// ---- batched elementwise kernels (grid.y = instance) ---------------------
+// Each block (x, instance) strides over the instance's M x M elements, so
+// that a small instance costs a few blocks instead of one per row of the
+// largest.
 namespace {
 __global__ void batch_x_to_d64_kernel(const BatchItem* items) {
-  const BatchItem& it = items[blockIdx.z];
-  const int i = blockIdx.y;
-  if (i >= it.M) return;
+  const BatchItem& it = items[blockIdx.y];
   const float* src = it.st->parity ? it.X[1] : it.X[0];
   const double th = it.st->theta;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x) {
+  const size_t n = (size_t)it.M * it.M;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / it.M), j = (int)(e % it.M);
     double v = (double)src[(size_t)(i < j ? i : j) * it.Mp + (i < j ? j : i)];
     if (i == j) v += th;
-    it.D64[0][(size_t)i * it.M + j] = v;
+    it.D64[0][e] = v;
   }
 }
 
 template <typename O>
 __global__ void batch_copy_out_kernel(const BatchItem* items, int from_x) {
-  const BatchItem& it = items[blockIdx.z];
-  const int i = blockIdx.y;
-  if (i >= it.M) return;
+  const BatchItem& it = items[blockIdx.y];
   O* out = (O*)it.D_out;
   const int p = it.st->parity;
-  if (from_x) {
-    const float* src = it.X[p];
-    const double th = it.st->theta;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x) {
-      double v = (double)src[(size_t)i * it.Mp + j];
+  const size_t n = (size_t)it.M * it.M;
+  const float* srcx = it.X[p];
+  const double* srcd = it.D64[p];
+  const double th = it.st->theta;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / it.M), j = (int)(e % it.M);
+    double v;
+    if (from_x) {
+      v = (double)srcx[(size_t)i * it.Mp + j];
       if (i == j) v += th;
-      out[(size_t)i * it.ldd + j] = (O)v;
+    } else {
+      v = srcd[e];
     }
-  } else {
-    const double* src = it.D64[p];
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x)
-      out[(size_t)i * it.ldd + j] = (O)src[(size_t)i * it.M + j];
+    out[(size_t)i * it.ldd + j] = (O)v;
   }
 }
 
@@ -742,6 +774,11 @@ void launch_batch_any_active(const BatchItem* items, int batch, unsigned long lo
                                             use_cond, active_out);
 }
 
+void launch_batch_check_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
+                                cudaStream_t s) {
+  batch_check_control_kernel<<<batch, kCtlThreads, 0, s>>>(part, items, ctl);
+}
+
 void launch_batch_state_init(const BatchItem* items, int batch, int phase, cudaStream_t s) {
   batch_state_init_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, phase);
 }
@@ -750,14 +787,20 @@ void launch_batch_phase_begin(const BatchItem* items, int batch, int phase, cuda
   batch_phase_begin_kernel<<<(batch + 127) / 128, 128, 0, s>>>(items, batch, phase);
 }
 
+// blocks per instance of the batched elementwise kernels
+inline int ew_blocks(int maxM) {
+  const long long b = ((long long)maxM * maxM + 8191) / 8192;  // ~32 elements a thread
+  return (int)(b < 1 ? 1 : (b > 64 ? 64 : b));
+}
+
 void launch_batch_x_to_d64(const BatchItem* items, int batch, int maxM, cudaStream_t s) {
-  dim3 g((maxM + 255) / 256 < 4 ? (maxM + 255) / 256 : 4, maxM, batch);
+  dim3 g(ew_blocks(maxM), batch);
   batch_x_to_d64_kernel<<<g, 256, 0, s>>>(items);
 }
 
 void launch_batch_copy_out(const BatchItem* items, int batch, int maxM, int from_x, int out_f64,
                            cudaStream_t s) {
-  dim3 g((maxM + 255) / 256 < 4 ? (maxM + 255) / 256 : 4, maxM, batch);
+  dim3 g(ew_blocks(maxM), batch);
   if (out_f64)
     batch_copy_out_kernel<double><<<g, 256, 0, s>>>(items, from_x);
   else

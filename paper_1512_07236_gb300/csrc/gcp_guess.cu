@@ -382,13 +382,14 @@ __global__ void __launch_bounds__(kGuessThreads) batch_guess_finalize_kernel(
 
 template <typename T, bool BF16>
 __global__ void batch_guess_write_x_kernel(const BatchItem* items, float scale) {
-  const BatchItem& it = items[blockIdx.z];
-  const int i = blockIdx.y;
-  if (i >= it.Mp) return;
+  const BatchItem& it = items[blockIdx.y];
   const T* H = (const T*)it.H;
   const double beta2 = it.st->beta2, mu = it.st->mu;
   using HT = typename Split<BF16>::T;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.Mp; j += gridDim.x * blockDim.x) {
+  const size_t n = (size_t)it.Mp * it.Mp;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / it.Mp), j = (int)(e % it.Mp);
     double v = 0.0;
     if (i < it.M && j < it.M) {
       // the upper triangle of H only (exactly symmetric split state)
@@ -407,15 +408,16 @@ __global__ void batch_guess_write_x_kernel(const BatchItem* items, float scale) 
 
 template <typename T>
 __global__ void batch_guess_write_d_kernel(const BatchItem* items) {
-  const BatchItem& it = items[blockIdx.z];
-  const int i = blockIdx.y;
-  if (i >= it.M) return;
+  const BatchItem& it = items[blockIdx.y];
   const T* H = (const T*)it.H;
   const double beta2 = it.st->beta2, mu = it.st->mu, theta = it.st->theta;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < it.M; j += gridDim.x * blockDim.x) {
+  const size_t n = (size_t)it.M * it.M;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / it.M), j = (int)(e % it.M);
     double v = -beta2 * (double)H[(size_t)i * it.ld + j];
     if (i == j) v += theta + beta2 * mu;
-    it.D64[0][(size_t)i * it.M + j] = v;
+    it.D64[0][e] = v;
   }
 }
 }  // namespace
@@ -434,9 +436,14 @@ void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, 
   else
     batch_guess_finalize_kernel<float><<<batch, kGuessThreads, 0, s>>>(items, gpart, gstride,
                                                                        guess_mode);
+  // blocks per instance: ~32 elements a thread for the largest instance
+  auto ew = [](long long n) {
+    const long long b = (n + 8191) / 8192;
+    return (int)(b < 1 ? 1 : (b > 64 ? 64 : b));
+  };
   if (split) {
     const int maxMp = ((maxM + 255) / 256) * 256;
-    dim3 g((maxMp + 255) / 256 < 4 ? (maxMp + 255) / 256 : 4, maxMp, batch);
+    dim3 g(ew((long long)maxMp * maxMp), batch);
     if (bf16) {
       if (h_f64)
         batch_guess_write_x_kernel<double, true><<<g, 256, 0, s>>>(items, split_scale);
@@ -449,7 +456,7 @@ void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, 
         batch_guess_write_x_kernel<float, false><<<g, 256, 0, s>>>(items, split_scale);
     }
   } else {
-    dim3 g((maxM + 255) / 256 < 4 ? (maxM + 255) / 256 : 4, maxM, batch);
+    dim3 g(ew((long long)maxM * maxM), batch);
     if (h_f64)
       batch_guess_write_d_kernel<double><<<g, 256, 0, s>>>(items);
     else

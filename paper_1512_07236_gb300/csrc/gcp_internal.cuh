@@ -103,14 +103,15 @@ struct BatchItem {
   int gblocks;         // reduction blocks of the guess/energy passes
                        // (guess_partial_blocks(M): the single-solve layout)
   // exact-slice refinement (mixed modes): digit slices, row scales of D and
-  // of X = S - D, fp16 halves of both, and 13 tensor maps (the 9 slices with
-  // 64-wide boxes, then D hi, D lo, X hi, X lo with 32-wide boxes)
+  // of X = S - D, fp16 halves of both, and 15 tensor maps (the 9 slices with
+  // 64-wide boxes, then D hi, D lo, X hi, X lo, slice 0 and slice 1 with
+  // 32-wide boxes: the operands of the stop-test product)
   void* oz_sl[kOzSlices];
   double* oz_rs;
   double* oz_xs;
   void *oz_dh, *oz_dl, *oz_xh, *oz_xl;
   const void* oz_maps;
-  int oz_off;  // first partial-sum slot (min(M, 1024) slots, as a single solve)
+  int oz_off;  // first partial-sum slot (oz_finalize_blocks(M) slots, as a single solve)
 };
 
 // ---- guess (gcp_guess.cu) ------------------------------------------------
@@ -251,7 +252,12 @@ int oz_num_products(int M, int wcap);
 // Partials (Tr D, Tr S, sum S o D, ||S - D||^2, 0) per block for the control
 // kernel, and the fp16 halves of xscale_i X_ij, X = S - D, with a power of
 // two xscale_i per row (max_j |xscale_i X_ij| < 2^13).
-int oz_finalize_blocks(int M);
+// Blocks of the finalize pass (eight rows at a time, one warp each), and so
+// its partial-sum slots: single solves and every instance of a batch alike.
+__host__ __device__ inline int oz_finalize_blocks(int M) {
+  const int b = (M + 7) / 8;
+  return b < 1024 ? b : 1024;
+}
 // fp16 halves (Mp x Mp, zero padded) of kRefScale D, of s Delta with
 // s = check_delta_scale(State::R) and of kRefScale Delta, Delta = D1 - D.
 void launch_check_halves(const double* D64, const double* D1, int M, int Mp, void* Dh, void* Dl,
@@ -269,6 +275,9 @@ int launch_batch_oz_gemm(const BatchItem* items, const int* tile_inst, int ntile
                          int wcap, cudaStream_t s);
 void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
                               cudaStream_t s);
+// Operands of the batched stop-test product (as launch_check_halves per
+// instance: D = D64[parity ^ 1], D1 = D64[parity]).
+void launch_batch_check_halves(const BatchItem* items, int batch, int maxM, cudaStream_t s);
 size_t oz_batch_map_bytes();
 int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int errlen);
 
@@ -302,6 +311,10 @@ void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, 
                         cudaStream_t s);
 void launch_batch_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
                           cudaStream_t s);
+// Stop test after a batched refinement step from the check product's tile
+// partials of each instance (as launch_check_control of a single solve).
+void launch_batch_check_control(const double* part, const BatchItem* items, int batch, Ctl ctl,
+                                cudaStream_t s);
 void launch_batch_any_active(const BatchItem* items, int batch, unsigned long long cond,
                              int use_cond, int* active_out, cudaStream_t s);
 void launch_batch_state_init(const BatchItem* items, int batch, int phase, cudaStream_t s);

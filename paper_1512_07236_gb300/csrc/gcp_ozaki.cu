@@ -194,77 +194,59 @@ __global__ void __launch_bounds__(256) batch_oz_slice_kernel(const BatchItem* it
 // the diagonal of X do not depend on which digit pairs the slice product
 // kept (its dropped squares are all positive on the diagonal).
 constexpr int kFinThreads = 256;
-constexpr int kFinCache = 32;
-// Block `blk` of `nblk`: rows blk, blk + nblk, ...; partials into part[0..5].
+constexpr int kFinWarps = kFinThreads / 32;
+constexpr int kFinCache = 32;  // values of a row a lane keeps: 1024 columns per warp
+// One warp per row: warp w of block `blk` of `nblk` takes rows
+// blk kFinWarps + w, then every nblk kFinWarps; partials into part[0..5].
 __device__ __forceinline__ void finalize_rows(double* __restrict__ S,
                                               const double* __restrict__ D, int M, int Mp,
                                               int blk, int nblk, double* __restrict__ part,
                                               __half* __restrict__ Xh, __half* __restrict__ Xl,
                                               double* __restrict__ xscale) {
   __shared__ double red[32 * 5];
-  __shared__ float mred[32];
-  __shared__ double dred[kFinThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const int gw = blk * kFinWarps + (threadIdx.x >> 5), nw = nblk * kFinWarps;
   double v0 = 0.0, v1 = 0.0, v2 = 0.0;  // Tr D, Tr S, sum S o D
   float v3 = 0.f;                       // ||S - D||_F^2
-  for (int i = blk; i < Mp; i += nblk) {
+  for (int i = gw; i < Mp; i += nw) {
     float xc[kFinCache];
     float mx = 0.f;
     double sii = 0.0;  // (D^2)_ii in FP64
-    if (i < M) {  // uniform over the block
+    if (i < M) {
       double a = 0.0;
-      for (int j = threadIdx.x; j < M; j += kFinThreads) {
+      for (int j = lane; j < M; j += 32) {
         const double d = D[(size_t)i * M + j];
         a = fma(d, d, a);
       }
-      a = warp_sum(a);
-      if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = a;
-      __syncthreads();
-      for (int w = 0; w < kFinThreads / 32; ++w) sii += dred[w];
-      __syncthreads();  // dred is reused by the next row
+      sii = warp_sum(a);
     }
+    auto element = [&](int j) -> float {
+      const size_t o = (size_t)i * M + j;
+      const double sv = i == j ? sii : S[o], dv = D[o];
+      if (i == j) {
+        S[o] = sii;
+        v0 += dv;
+        v1 += sv;
+      }
+      v2 += sv * dv;
+      const float x = (float)(sv - dv);
+      v3 = fmaf(x, x, v3);
+      mx = fmaxf(mx, fabsf(x));
+      return x;
+    };
 #pragma unroll
     for (int k = 0; k < kFinCache; ++k) {
-      const int j = threadIdx.x + k * kFinThreads;
-      xc[k] = 0.f;
-      if (i < M && j < M) {
-        const size_t o = (size_t)i * M + j;
-        const double sv = i == j ? sii : S[o], dv = D[o];
-        if (i == j) {
-          S[o] = sii;
-          v0 += dv;
-          v1 += sv;
-        }
-        v2 += sv * dv;
-        const float x = (float)(sv - dv);
-        xc[k] = x;
-        v3 = fmaf(x, x, v3);
-        mx = fmaxf(mx, fabsf(x));
-      }
+      const int j = lane + 32 * k;
+      xc[k] = (i < M && j < M) ? element(j) : 0.f;
     }
     if (i < M)
-      for (int j = threadIdx.x + kFinCache * kFinThreads; j < M; j += kFinThreads) {
-        const size_t o = (size_t)i * M + j;
-        const double sv = i == j ? sii : S[o], dv = D[o];
-        if (i == j) {
-          S[o] = sii;
-          v0 += dv;
-          v1 += sv;
-        }
-        v2 += sv * dv;
-        const float x = (float)(sv - dv);
-        v3 = fmaf(x, x, v3);
-        mx = fmaxf(mx, fabsf(x));
-      }
+      for (int j = lane + 32 * kFinCache; j < M; j += 32) element(j);
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    float m = 0.f;
-    for (int w = 0; w < kFinThreads / 32; ++w) m = fmaxf(m, mred[w]);
-    __syncthreads();  // mred is reused by the next row
     int e = 0;
-    if (m > 0.f) frexpf(m, &e);  // m < 2^e
+    if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
     const float sx = ldexpf(1.0f, 13 - e);
-    if (threadIdx.x == 0) xscale[i] = (double)sx;
+    if (lane == 0) xscale[i] = (double)sx;
     auto put = [&](int j, float x) {
       const float y = x * sx;  // exact: a power of two
       const __half h = __float2half_rn(y);
@@ -273,10 +255,10 @@ __device__ __forceinline__ void finalize_rows(double* __restrict__ S,
     };
 #pragma unroll
     for (int k = 0; k < kFinCache; ++k) {
-      const int j = threadIdx.x + k * kFinThreads;
+      const int j = lane + 32 * k;
       if (j < Mp) put(j, xc[k]);
     }
-    for (int j = threadIdx.x + kFinCache * kFinThreads; j < Mp; j += kFinThreads) {
+    for (int j = lane + 32 * kFinCache; j < Mp; j += 32) {
       float x = 0.f;
       if (i < M && j < M) {
         const size_t o = (size_t)i * M + j;
@@ -299,16 +281,14 @@ __device__ __forceinline__ void finalize_rows(double* __restrict__ S,
 // and of kRefScale Delta: D Delta, Delta D and Delta (kRefScale Delta) then
 // share the scale kRefScale s and one accumulator.  The last operand loses
 // Delta's smallest entries to subnormals, an error of second order.
-__global__ void __launch_bounds__(256) check_halves_kernel(
+__device__ __forceinline__ void check_halves_range(
     const double* __restrict__ D, const double* __restrict__ D1, int M, int Mp,
     __half* __restrict__ Dh, __half* __restrict__ Dl, __half* __restrict__ Xh,
     __half* __restrict__ Xl, __half* __restrict__ Eh, __half* __restrict__ El,
-    const State* __restrict__ st) {
-  if (st->stopped) return;
+    const State* __restrict__ st, size_t first, size_t stride) {
   const float sd = (float)check_delta_scale(st->R);  // a power of two
   const size_t n = (size_t)Mp * Mp;
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
-       o += (size_t)gridDim.x * blockDim.x) {
+  for (size_t o = first; o < n; o += stride) {
     const int i = (int)(o / Mp), j = (int)(o % Mp);
     double d = 0.0, dd = 0.0;
     if (i < M && j < M) {
@@ -327,6 +307,29 @@ __global__ void __launch_bounds__(256) check_halves_kernel(
   }
 }
 
+__global__ void __launch_bounds__(256) check_halves_kernel(
+    const double* __restrict__ D, const double* __restrict__ D1, int M, int Mp,
+    __half* __restrict__ Dh, __half* __restrict__ Dl, __half* __restrict__ Xh,
+    __half* __restrict__ Xl, __half* __restrict__ Eh, __half* __restrict__ El,
+    const State* __restrict__ st) {
+  if (st->stopped) return;
+  check_halves_range(D, D1, M, Mp, Dh, Dl, Xh, Xl, Eh, El, st,
+                     (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+// Batched: block (x, instance) over the instance's Mp x Mp elements; the
+// refinement step read D64[parity ^ 1] and wrote D1 = D64[parity].
+__global__ void __launch_bounds__(256) batch_check_halves_kernel(const BatchItem* items) {
+  const BatchItem& it = items[blockIdx.y];
+  const State* st = it.st;
+  if (st->stopped) return;
+  const int par = st->parity;
+  check_halves_range(it.D64[par ^ 1], it.D64[par], it.M, it.Mp, (__half*)it.oz_dh,
+                     (__half*)it.oz_dl, (__half*)it.oz_xh, (__half*)it.oz_xl,
+                     (__half*)it.oz_sl[0], (__half*)it.oz_sl[1], st,
+                     (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
 __global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
     double* __restrict__ S, const double* __restrict__ D, int M, int Mp,
     double* __restrict__ part, __half* __restrict__ Xh, __half* __restrict__ Xl,
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(kFinThreads) oz_finalize_kernel(
 __global__ void __launch_bounds__(kFinThreads) batch_oz_finalize_kernel(const BatchItem* items,
                                                                         double* __restrict__ part) {
   const BatchItem& it = items[blockIdx.y];
-  const int nblk = it.M < 1024 ? it.M : 1024;
+  const int nblk = oz_finalize_blocks(it.M);
   if ((int)blockIdx.x >= nblk || it.st->stopped) return;
   finalize_rows(it.S64, it.D64[it.st->parity], it.M, it.Mp, blockIdx.x, nblk,
                 part + (size_t)(it.oz_off + blockIdx.x) * kPartFields, (__half*)it.oz_xh,
@@ -770,23 +773,22 @@ void launch_batch_oz_slice(const BatchItem* items, int batch, int maxM, cudaStre
 
 void launch_batch_oz_finalize(const BatchItem* items, int batch, int maxM, double* part,
                               cudaStream_t s) {
-  dim3 g(maxM < 1024 ? maxM : 1024, batch);
+  dim3 g(oz_finalize_blocks(maxM), batch);
   batch_oz_finalize_kernel<<<g, kFinThreads, 0, s>>>(items, part);
 }
 
-size_t oz_batch_map_bytes() { return (kOzSlices + 4) * sizeof(CUtensorMap); }
+size_t oz_batch_map_bytes() { return (kOzSlices + 6) * sizeof(CUtensorMap); }
 
 int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int errlen) {
   CUtensorMap* m = (CUtensorMap*)maps_host;
   for (int k = 0; k < kOzSlices; ++k)
     if (tc_encode_map(&m[k], it.oz_sl[k], it.Mp, 0, err, errlen, BK)) return 1;
-  const void* halves[4] = {it.oz_dh, it.oz_dl, it.oz_xh, it.oz_xl};
-  for (int k = 0; k < 4; ++k)
+  const void* halves[6] = {it.oz_dh, it.oz_dl, it.oz_xh, it.oz_xl, it.oz_sl[0], it.oz_sl[1]};
+  for (int k = 0; k < 6; ++k)
     if (tc_encode_map(&m[kOzSlices + k], halves[k], it.Mp, 0, err, errlen)) return 1;
   return 0;
 }
 
-int oz_finalize_blocks(int M) { return M < 1024 ? M : 1024; }
 
 void launch_check_halves(const double* D64, const double* D1, int M, int Mp, void* Dh, void* Dl,
                          void* Xh, void* Xl, void* Eh, void* El, const State* st,
@@ -795,6 +797,13 @@ void launch_check_halves(const double* D64, const double* D1, int M, int Mp, voi
   const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   check_halves_kernel<<<grid, 256, 0, s>>>(D64, D1, M, Mp, (__half*)Dh, (__half*)Dl, (__half*)Xh,
                                            (__half*)Xl, (__half*)Eh, (__half*)El, st);
+}
+
+void launch_batch_check_halves(const BatchItem* items, int batch, int maxM, cudaStream_t s) {
+  const long long n = (long long)tc_pad(maxM) * tc_pad(maxM);
+  long long b = (n + 8191) / 8192;  // ~32 elements a thread for the largest instance
+  b = b < 1 ? 1 : (b > 64 ? 64 : b);
+  batch_check_halves_kernel<<<dim3((unsigned)b, batch), 256, 0, s>>>(items);
 }
 
 void launch_oz_finalize(double* S64, const double* D64, int M, int Mp, double* part,

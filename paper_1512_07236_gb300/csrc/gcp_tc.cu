@@ -511,6 +511,19 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
       c.al = &maps[2 * (par ^ 1) + 1];
       c.bh = &maps[4];
       c.bl = &maps[5];
+    } else if (MODE == 4) {
+      // stop-test product after a refinement step: A = D (halves at
+      // kRefScale), B = s Delta, the third segment's B = kRefScale Delta
+      // (slices 0 and 1); D1 = D64[par], the step's output
+      const CUtensorMap* om = (const CUtensorMap*)it.oz_maps;
+      c.ah = &om[kOzSlices];
+      c.al = &om[kOzSlices + 1];
+      c.bh = &om[kOzSlices + 2];
+      c.bl = &om[kOzSlices + 3];
+      c.ep.emaps = &om[kOzSlices + 4];
+      c.ep.S64 = it.S64;
+      c.ep.D64 = it.D64[par];
+      c.ep.ld64 = it.M;
     } else {
       // refinement product (X = S - D) D: the iterate just evaluated is
       // par^1 (the control kernel flipped the parity), the step writes par
@@ -1207,11 +1220,13 @@ int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int*
   if (mode == 1)
     return bf16 ? launch_tc<1, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
                 : launch_tc<1, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
-  if (mode == 3) {
-    // refinement product: fp16 halves, scales carried by the operands
+  if (mode == 3 || mode == 4) {
+    // refinement and stop-test products: fp16 halves, scales carried by the
+    // operands
     ep.split_scale = 1.0f;
     ep.inv_s2 = 1.0f;
-    return launch_tc<3, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
+    return mode == 3 ? launch_tc<3, false, true>(nullptr, nullptr, ep, items, tile_inst, s)
+                     : launch_tc<4, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
   }
   return bf16 ? launch_tc<2, true, true>(nullptr, nullptr, ep, items, tile_inst, s)
               : launch_tc<2, false, true>(nullptr, nullptr, ep, items, tile_inst, s);
