@@ -496,55 +496,78 @@ def _sym(A):
     return 0.5 * (A + A.T)
 
 
-def step_adjoint(D, G, T1, T2, c):
-    """Pull G = dL/dD_{n+1} back through D_{n+1} = aD + bD^2 - 2D^3 with
-    a = 1-2c, b = 2+2c and c = (T2-T3)/(T1-T2) a function of D:
-      polynomial part: aG + b(GD + DG) - 2(GD^2 + DGD + D^2G)
-      c part: s * dc/dD, s = dL/dc = sum G o (2D^2 - 2D),
+def _step_coefficients(c, method):
+    """(a, b, g3) of D+ = a D + b D^2 + g3 D^3 for c and the method, and
+    their derivatives with respect to c.
+      HPCP (Eq. hpcp3): a = 1 - 2c, b = 2 + 2c, g3 = -2.
+      PMCP (Eq. pm1):   c <= 1/2: a = (1-2c)/(1-c), b = (1+c)/(1-c),
+                                  g3 = -1/(1-c);
+                        c >  1/2: a = 0, b = (1+c)/c, g3 = -1/c."""
+    if method == "pmcp":
+        if c <= 0.5:
+            k = 1.0 - c
+            return ((1.0 - 2.0 * c) / k, (1.0 + c) / k, -1.0 / k,
+                    -1.0 / k ** 2, 2.0 / k ** 2, -1.0 / k ** 2)
+        return 0.0, (1.0 + c) / c, -1.0 / c, 0.0, -1.0 / c ** 2, 1.0 / c ** 2
+    return 1.0 - 2.0 * c, 2.0 + 2.0 * c, -2.0, -2.0, 2.0, 0.0
+
+
+def step_adjoint(D, G, T1, T2, c, method="hpcp"):
+    """Pull G = dL/dD_{n+1} back through D_{n+1} = aD + bD^2 + g3 D^3 with
+    the coefficients of the method (``_step_coefficients``) and
+    c = (T2-T3)/(T1-T2) a function of D (Eq. mcwgamb):
+      polynomial part: aG + b(GD + DG) + g3(GD^2 + DGD + D^2G)
+      c part: s * dc/dD, s = dL/dc = sum G o (a'D + b'D^2 + g3'D^3),
               dc/dD = [(2D - 3D^2) - c(I - 2D)] / (T1 - T2).
     Returns the symmetric dL/dD_n."""
     M = D.shape[0]
     I = np.eye(M)
-    a = 1.0 - 2.0 * c
-    b = 2.0 + 2.0 * c
+    a, b, g3, da, db, dg3 = _step_coefficients(c, method)
     D2 = D @ D
-    poly = a * G + b * (G @ D + D @ G) - 2.0 * (G @ D2 + D @ G @ D + D2 @ G)
-    s = float(np.sum(G * (2.0 * D2 - 2.0 * D)))
+    D3 = D2 @ D
+    poly = a * G + b * (G @ D + D @ G) + g3 * (G @ D2 + D @ G @ D + D2 @ G)
+    s = float(np.sum(G * (da * D + db * D2 + dg3 * D3)))
     dc = ((2.0 * D - 3.0 * D2) - c * (I - 2.0 * D)) / (T1 - T2)
     return _sym(poly + s * dc)
 
 
-def guess_adjoint(H, N, G0):
-    """Pull G0 = dL/dD_0 back through the guess (Eqs. dmguess, pmcpguess):
-    D_0 = theta I + beta2 (mu I - H), mu = Tr H / M, beta2 the smaller of
-    theta/(H_max - mu) and thetabar/(mu - H_min), H_max/H_min from the
-    Gershgorin row of the extreme disc (a subgradient at |H_ij| = 0).
-    Returns the symmetric dL/dH."""
+def _branch_guess_adjoint(H, N, G0, which):
+    """Pull G0 = dL/dD_0 back through D_0 = theta I + b (mu I - H) with
+    b = beta_min ("min": the canonical guess, Eqs. dmguess and pmcpguess) or
+    b = beta_max ("max": I - Dbar_0 of the hole guess), mu = Tr H / M,
+    beta_min / beta_max the smaller / larger of theta/(H_max - mu) and
+    thetabar/(mu - H_min), H_max/H_min from the Gershgorin row of the
+    extreme disc (a subgradient at |H_ij| = 0).  Returns the symmetric
+    dL/dH."""
     H = np.asarray(H, dtype=np.float64)
     M = H.shape[0]
     _, info = canonical_guess(H, N)
-    theta, mu, beta2 = info["theta"], info["mu"], info["beta2"]
+    theta, mu = info["theta"], info["mu"]
     hmin, hmax = info["hmin"], info["hmax"]
-    I = np.eye(M)
-    gH = -beta2 * G0
-    g_mu = beta2 * float(np.trace(G0))
-    g_beta2 = float(np.sum(G0 * (mu * I - H)))
-    diag = np.diag(H)
-    r = np.abs(H).sum(axis=1) - np.abs(diag)
     b_up = theta / (hmax - mu) if hmax - mu > 0 else math.inf
     b_lo = (1 - theta) / (mu - hmin) if mu - hmin > 0 else math.inf
-    if b_up <= b_lo:
-        # beta2 = theta / (hmax - mu)
-        g_mu += g_beta2 * theta / (hmax - mu) ** 2
-        g_hmax = -g_beta2 * theta / (hmax - mu) ** 2
+    use_up = b_up <= b_lo
+    if which == "max" and math.isfinite(max(b_up, b_lo)):
+        use_up = not use_up
+    b = b_up if use_up else b_lo
+    I = np.eye(M)
+    gH = -b * G0
+    g_mu = b * float(np.trace(G0))
+    g_b = float(np.sum(G0 * (mu * I - H)))
+    diag = np.diag(H)
+    r = np.abs(H).sum(axis=1) - np.abs(diag)
+    if use_up:
+        # b = theta / (hmax - mu)
+        g_mu += g_b * theta / (hmax - mu) ** 2
+        g_hmax = -g_b * theta / (hmax - mu) ** 2
         i = int(np.argmax(diag + r))
         row = np.sign(H[i, :])
         row[i] = 1.0
         gH[i, :] += g_hmax * row
     else:
-        # beta2 = thetabar / (mu - hmin)
-        g_mu += -g_beta2 * (1 - theta) / (mu - hmin) ** 2
-        g_hmin = g_beta2 * (1 - theta) / (mu - hmin) ** 2
+        # b = thetabar / (mu - hmin)
+        g_mu += -g_b * (1 - theta) / (mu - hmin) ** 2
+        g_hmin = g_b * (1 - theta) / (mu - hmin) ** 2
         i = int(np.argmin(diag - r))
         row = -np.sign(H[i, :])
         row[i] = 1.0
@@ -553,15 +576,57 @@ def guess_adjoint(H, N, G0):
     return _sym(gH)
 
 
-def reverse_mode_grad(H, N, n_iter, G_D=None, g_E=0.0):
-    """dL/dH for L = <G_D, D_K> + g_E * Tr(D_K H), D_K after exactly
-    ``n_iter`` steps of Eq. hpcp3 from the guess.  Plain reverse mode: the
-    forward pass stores every iterate, the backward pass applies
-    ``step_adjoint`` in reverse and ``guess_adjoint`` last.  Returns
-    (dL/dH symmetric, forward result dict)."""
+def guess_adjoint(H, N, G0, guess="canonical"):
+    """Pull G0 = dL/dD_0 back through the guess.  "canonical" and "hole"
+    are the two branches of ``_branch_guess_adjoint``.  "hpcp+" (Eq. hpcpguess)
+    is D_0 = alpha A + (1 - alpha) B with A the canonical guess and
+    B = I - Dbar_0: at fixed alpha the weighted branch adjoints, and where
+    alpha is the root of q(alpha, H) = Tr(D_0^2) - target = 0 of
+    Eq. hpcpguessalpha (not clamped, not the fixed 1/2 of the middle
+    fillings) the implicit derivative dalpha/dH = -(dq/dH) / (dq/dalpha),
+    dq/dalpha = 2 Tr(D_0 (A - B)), dq/dH = 2 (alpha adj_A(D_0) +
+    (1 - alpha) adj_B(D_0)).  Returns the symmetric dL/dH."""
+    if guess == "canonical":
+        return _branch_guess_adjoint(H, N, G0, "min")
+    if guess == "hole":
+        return _branch_guess_adjoint(H, N, G0, "max")
+    if guess != "hpcp+":
+        raise ValueError("unknown guess")
     H = np.asarray(H, dtype=np.float64)
     M = H.shape[0]
-    D, _ = canonical_guess(H, N)
+    D0, info = hpcp_plus_guess(H, N)
+    alpha = info["alpha"]
+    A, _ = canonical_guess(H, N)
+    B = np.eye(M) - hole_guess(H, N)[0]
+    g = alpha * _branch_guess_adjoint(H, N, G0, "min") + \
+        (1.0 - alpha) * _branch_guess_adjoint(H, N, G0, "max")
+    theta, delta = N / M, 2.0 / 3.0
+    has_target = theta <= 1.0 - delta or theta >= delta
+    if has_target and 0.0 < alpha < 1.0:
+        dq_dalpha = 2.0 * float(np.sum(D0 * (A - B)))
+        dq_dH = 2.0 * (alpha * _branch_guess_adjoint(H, N, D0, "min")
+                       + (1.0 - alpha) * _branch_guess_adjoint(H, N, D0, "max"))
+        dL_dalpha = float(np.sum(G0 * (A - B)))
+        g = g - dL_dalpha * dq_dH / dq_dalpha
+    return _sym(g)
+
+
+def reverse_mode_grad(H, N, n_iter, G_D=None, g_E=0.0, guess="canonical", method="hpcp"):
+    """dL/dH for L = <G_D, D_K> + g_E * Tr(D_K H), D_K after exactly
+    ``n_iter`` steps of the method (Eq. hpcp3, or Eq. pm1 for "pmcp") from the
+    guess.  Plain reverse mode: the forward pass stores every iterate, the
+    backward pass applies ``step_adjoint`` in reverse and ``guess_adjoint``
+    last.  Returns (dL/dH symmetric, forward result dict)."""
+    H = np.asarray(H, dtype=np.float64)
+    M = H.shape[0]
+    if guess == "canonical":
+        D, _ = canonical_guess(H, N)
+    elif guess == "hpcp+":
+        D, _ = hpcp_plus_guess(H, N)
+    elif guess == "hole":
+        D, _ = hpcp_plus_guess(H, N, alpha=0.0)
+    else:
+        raise ValueError("unknown guess")
     Ds, aux = [], []
     for _ in range(n_iter):
         S = D @ D
@@ -575,15 +640,16 @@ def reverse_mode_grad(H, N, n_iter, G_D=None, g_E=0.0):
             continue
         c = (T2 - T3) / den
         aux.append((T1, T2, c))
-        D = (1 - 2 * c) * D + (2 + 2 * c) * S - 2.0 * (S @ D)
+        a, b, g3 = _step_coefficients(c, method)[:3]
+        D = a * D + b * S + g3 * (S @ D)
     DK = D
     G = np.zeros((M, M)) if G_D is None else np.array(G_D, dtype=np.float64)
     G = G + g_E * H
     for D_n, ax in zip(reversed(Ds), reversed(aux)):
         if ax is None:
             continue
-        G = step_adjoint(D_n, G, *ax)
-    gH = guess_adjoint(H, N, G) + g_E * _sym(DK)
+        G = step_adjoint(D_n, G, *ax, method=method)
+    gH = guess_adjoint(H, N, G, guess=guess) + g_E * _sym(DK)
     return gH, dict(D=DK, E=float(np.sum(DK * H)))
 
 

@@ -311,6 +311,45 @@ def _loss(H, N, n_iter, G):
     return float(np.sum(G * r["D"])) + r["E"]
 
 
+def _loss_gm(H, N, n_iter, G, guess, method):
+    r = o.solve(H, N, fixed_iters=n_iter, record=False, guess=guess, method=method)
+    return float(np.sum(G * r["D"])) + r["E"]
+
+
+@pytest.mark.parametrize("M,N,guess,method", [
+    (14, 4, "canonical", "pmcp"),   # c <= 1/2 branch of Eq. pm1
+    (14, 10, "canonical", "pmcp"),  # c > 1/2 branch
+    (15, 4, "hpcp+", "hpcp"),       # alpha an interior root of Eq. hpcpguessalpha
+    (15, 7, "hpcp+", "hpcp"),       # middle filling: alpha = 1/2
+    (15, 11, "hpcp+", "pmcp"),      # the other target, PM steps
+    (16, 8, "hole", "hpcp"),
+    (16, 8, "hole", "pmcp"),
+])
+def test_reverse_mode_guesses_and_pmcp_match_central_differences(M, N, guess, method):
+    """The adjoint of the PM step (both branches of Eq. pm1, through c_n) and
+    of the HPCP+ and hole guesses (through alpha and the Gershgorin branch
+    they use) against central differences of the oracle's own forward."""
+    H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.2), (0.2, 1.0), seed=21)
+    G = inputs.symmetric_gaussian(M, 0.3, seed=22)
+    K = 6
+    gH, fwd = o.reverse_mode_grad(H, N, K, G_D=G, g_E=1.0, guess=guess, method=method)
+    ref = o.solve(H, N, fixed_iters=K, guess=guess, method=method)["D"]
+    assert np.abs(fwd["D"] - ref).max() <= 1e-14
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for _ in range(6):
+        E = rng.standard_normal((M, M))
+        E = E + E.T
+        E /= np.linalg.norm(E)
+        fd = (_loss_gm(H + h * E, N, K, G, guess, method)
+              - _loss_gm(H - h * E, N, K, G, guess, method)) / (2 * h)
+        assert float(np.sum(gH * E)) == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    # every guess has Tr D_0 = N and both steps keep the trace: Tr D_K is
+    # constant, its gradient zero
+    gT, _ = o.reverse_mode_grad(H, N, K, G_D=np.eye(M), g_E=0.0, guess=guess, method=method)
+    assert np.abs(gT).max() <= 1e-11
+
+
 def test_reverse_mode_matches_central_differences():
     M, N, K = 14, 4, 6
     H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.2), (0.2, 1.0), seed=21)
