@@ -156,7 +156,7 @@ typedef struct {
  *                        the particle-hole duality of the recursion.  Its
  *                        spectrum leaves [0, 1] away from half filling,
  *                        where the solve reports GCP_ERR_ILL_CONDITIONED.
- * gcp_backward takes GCP_GUESS_CANONICAL only. */
+ * gcp_backward differentiates all three. */
 typedef enum {
   GCP_GUESS_CANONICAL = 0,
   GCP_GUESS_HPCP_PLUS = 1,
@@ -171,7 +171,7 @@ typedef enum {
  *                    same c_n (Eq. mcwgamb).
  * Both conserve Tr D.  The refinement steps of the mixed modes are the
  * McWeeny step with the trace-restoring c for either method.  gcp_backward
- * differentiates GCP_METHOD_HPCP only. */
+ * differentiates both (GCP_METHOD_PMCP with GCP_FP64). */
 typedef enum { GCP_METHOD_HPCP = 0, GCP_METHOD_PMCP = 1 } gcp_method;
 
 typedef struct {
@@ -256,6 +256,9 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
  * (D_K is symmetric, so only the symmetric part of G_D matters);
  * dL_dH: device M x M (ld, h_dtype), written, symmetric (the derivative with
  * respect to a symmetric H; the Gershgorin bound contributes a subgradient).
+ * opt->guess: any gcp_guess (the HPCP+ guess through its alpha, Eq.
+ * hpcpguessalpha); opt->method: GCP_METHOD_HPCP or GCP_METHOD_PMCP (Eq. pm1;
+ * GCP_FP64 only, GCP_ERR_UNSUPPORTED with GCP_FP32).
  * Runs the forward pass itself, keeping a checkpoint every opt->ckpt_every
  * steps (default 8) and recomputing the iterates in between; steps past the
  * 0/0 guard are identity steps.  0 < N < M required. */

@@ -3,7 +3,8 @@
 //
 // The function differentiated is L = <G_D, D_K> + g_E Tr(H D_K) with D_K
 // after exactly K steps of Eq. hpcp3 from the guess of Eq. dmguess /
-// Eq. pmcpguess, as in gcp_adjoint.cu, but every iterate lives in the split
+// Eq. pmcpguess (or the HPCP+ or hole guess), as in gcp_adjoint.cu, but every
+// iterate lives in the split
 // state of the tensor-core path (X = D - theta J in FP32 plus the fp16 halves
 // of 2^14 X, Sigma = D^2 - theta^2 J likewise) and c_n follows the rules of
 // the fixed-iteration split phase, recorded per step by the control kernel:
@@ -249,7 +250,7 @@ void adjoint_tc_free(void* ws) {
   delete w;
 }
 
-int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f64,
+int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f64, int guess,
                         const void* GD, double gE, void* dLdH, int K, int ck, State* st,
                         double* part, double* gpart, double* hist, float* scratch,
                         cudaStream_t s, char* err, int errlen) {
@@ -342,8 +343,7 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
 
   // ---------------- forward with checkpoints -----------------------------
   launch_guess_reduce(H, h_f64, M, ld, gpart, s);
-  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld, GCP_GUESS_CANONICAL,
-                        st, s);
+  launch_guess_finalize(gpart, guess_partial_blocks(M), M, N, H, h_f64, ld, guess, st, s);
   launch_state_init(st, 1, s);
   // the forward runs in the last two slots (ping-pong), Sigma in slot 0
   const int fa = ck - 1 < 0 ? 0 : ck - 1, fb = ck;
@@ -538,7 +538,8 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
   // ---------------- guess (FP64, shared with gcp_adjoint.cu) ---------------
   to_f64_kernel<<<rgrid(M, M), 256, 0, s>>>(w->G, Mp, M, w->G64);
   AT_CK(cudaPeekAtLastError());
-  return adjoint_guess(H, M, N, ld, h_f64, w->G64, w->DK, gE, dLdH, gpart, st, s, err, errlen);
+  return adjoint_guess(H, M, N, ld, h_f64, guess, w->G64, w->DK, gE, dLdH, gpart, st, s, err,
+                       errlen);
 #undef AT_TIMEOUT
 #undef AT_CK
 }

@@ -1239,9 +1239,12 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
   if (o.prec != GCP_FP64 && o.prec != GCP_FP32)
     return fail(h, GCP_ERR_UNSUPPORTED,
                 "gcp_backward: the adjoint runs in FP64 or FP32 (prec = GCP_FP64 or GCP_FP32)");
-  if (o.guess != GCP_GUESS_CANONICAL || o.method != GCP_METHOD_HPCP)
+  if (o.guess < GCP_GUESS_CANONICAL || o.guess > GCP_GUESS_HOLE ||
+      (o.method != GCP_METHOD_HPCP && o.method != GCP_METHOD_PMCP))
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_backward: bad guess or method");
+  if (o.prec == GCP_FP32 && o.method != GCP_METHOD_HPCP)
     return fail(h, GCP_ERR_UNSUPPORTED,
-                "gcp_backward: differentiates the canonical guess and HPCP steps only");
+                "gcp_backward: the FP32 adjoint differentiates HPCP steps only");
   cudaStream_t s = (cudaStream_t)o.stream;
   gcp_status r;
   if (o.prec == GCP_FP32) {
@@ -1252,8 +1255,8 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
     if ((r = ensure_common(h, nt, M, o.fixed_iters + 2)) != GCP_OK) return r;
     if ((r = ensure_tcs(h)) != GCP_OK) return r;
     char err[256] = {0};
-    const int rc = adjoint_backward_tc(&h->adj_tc, H, M, N, ld, h_dtype == GCP_F64, G_D, g_E,
-                                       dL_dH, o.fixed_iters, o.ckpt_every, h->st, h->part,
+    const int rc = adjoint_backward_tc(&h->adj_tc, H, M, N, ld, h_dtype == GCP_F64, o.guess, G_D,
+                                       g_E, dL_dH, o.fixed_iters, o.ckpt_every, h->st, h->part,
                                        h->gpart, h->hist, h->tcs, s, err, sizeof err);
     if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
     return GCP_OK;
@@ -1261,9 +1264,10 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
   if ((r = ensure_common(h, f64_num_tiles(M), M, o.fixed_iters + 2)) != GCP_OK) return r;
   if ((r = ensure_f64(h, M)) != GCP_OK) return r;
   char err[256] = {0};
-  const int rc = adjoint_backward(&h->adj, H, M, N, ld, h_dtype == GCP_F64, G_D, g_E, dL_dH,
-                                  o.fixed_iters, o.ckpt_every, h->D64[0], h->D64[1], h->S64,
-                                  h->part, h->gpart, h->st, h->hist, s, err, sizeof err);
+  const int rc = adjoint_backward(&h->adj, H, M, N, ld, h_dtype == GCP_F64, o.guess, o.method,
+                                  G_D, g_E, dL_dH, o.fixed_iters, o.ckpt_every, h->D64[0],
+                                  h->D64[1], h->S64, h->part, h->gpart, h->st, h->hist, s, err,
+                                  sizeof err);
   if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
   return GCP_OK;
 }

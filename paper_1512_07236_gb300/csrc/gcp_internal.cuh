@@ -283,20 +283,28 @@ int oz_build_batch_maps(void* maps_host, const BatchItem& it, char* err, int err
 
 // ---- adjoint (gcp_adjoint.cu) --------------------------------------------
 constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
-int adjoint_backward(void** ws, const void* H, int M, int N, int ld, int h_f64, const void* GD,
-                     double gE, void* dLdH, int K, int ck, double* D64_0, double* D64_1,
-                     double* S64, double* part, double* gpart, State* st, double* hist,
-                     cudaStream_t s, char* err, int errlen);
+// guess: gcp_guess of the forward; method: gcp_method of its steps.
+int adjoint_backward(void** ws, const void* H, int M, int N, int ld, int h_f64, int guess,
+                     int method, const void* GD, double gE, void* dLdH, int K, int ck,
+                     double* D64_0, double* D64_1, double* S64, double* part, double* gpart,
+                     State* st, double* hist, cudaStream_t s, char* err, int errlen);
 void adjoint_free(void* ws);
+// Coefficients (a, b, g3) of one step D+ = a D + b D^2 + g3 D^3 and their
+// derivatives with respect to c_n.
+struct StepCoeffs {
+  double a, b, g3, da, db, dg3;
+};
+StepCoeffs step_coeffs(double c, int method);
 // The guess part of the adjoint: dL/dH from G0 = dL/dD_0 and D_K (FP64,
-// M x M), written to dLdH (ld, h dtype).
-int adjoint_guess(const void* H, int M, int N, int ld, int h_f64, const double* G0,
+// M x M), written to dLdH (ld, h dtype); guess: gcp_guess.
+int adjoint_guess(const void* H, int M, int N, int ld, int h_f64, int guess, const double* G0,
                   const double* DK, double gE, void* dLdH, double* gpart, State* st,
                   cudaStream_t s, char* err, int errlen);
 // The same derivative with the iterates in the split state and the
-// products on the tensor cores (FP32; gcp_adjoint_tc.cu).  scratch:
-// tc_scratch_bytes() for the tensor-core kernels; hist: >= K + 2 records.
-int adjoint_backward_tc(void** ws, const void* H, int M, int N, int ld, int h_f64,
+// products on the tensor cores (FP32, HPCP steps; gcp_adjoint_tc.cu).
+// scratch: tc_scratch_bytes() for the tensor-core kernels; hist: >= K + 2
+// records.
+int adjoint_backward_tc(void** ws, const void* H, int M, int N, int ld, int h_f64, int guess,
                         const void* GD, double gE, void* dLdH, int K, int ck, State* st,
                         double* part, double* gpart, double* hist, float* scratch,
                         cudaStream_t s, char* err, int errlen);

@@ -255,11 +255,12 @@ class Solver:
         return outs, infos
 
     def backward(self, H, N, fixed_iters, G_D=None, g_E=0.0, ckpt_every=8, out=None,
-                 prec="fp64"):
+                 prec="fp64", guess="canonical", method="hpcp"):
         """dL/dH of L = <G_D, D_K> + g_E Tr(H D_K), D_K after exactly
         `fixed_iters` steps from the guess (gcp_backward).  prec "fp64": the
         FP64 recursion and adjoint; "fp32": the split-FP16 tensor-core
-        recursion (the iterates of prec="fp32" solves) and its adjoint."""
+        recursion (the iterates of prec="fp32" solves) and its adjoint.
+        guess / method: those of the forward (solve's options)."""
         _check_matrix(H, "H")
         if G_D is not None:
             _check_matrix(G_D, "G_D")
@@ -270,7 +271,8 @@ class Solver:
         _check_matrix(out, "out")
         if out.dtype != H.dtype or out.stride(0) != H.stride(0):
             raise ValueError("out must match H's dtype and layout")
-        o = make_options(prec=prec, fixed_iters=fixed_iters, ckpt_every=ckpt_every)
+        o = make_options(prec=prec, fixed_iters=fixed_iters, ckpt_every=ckpt_every, guess=guess,
+                         method=method)
         st = self.lib.gcp_backward(self.h, C.c_void_p(H.data_ptr()), H.shape[0], int(N),
                                    H.stride(0), _dtype_code(H),
                                    C.c_void_p(G_D.data_ptr() if G_D is not None else 0),

@@ -104,8 +104,10 @@ def test_batched_rejects(lib, handle):
     (dict(fixed_iters=0), gcp.ERR_INVALID_ARG),
     (dict(fixed_iters=5, prec=gcp.PRECISIONS["mixed_fp16"]), gcp.ERR_UNSUPPORTED),
     (dict(fixed_iters=5, prec=gcp.PRECISIONS["fp16x3"]), gcp.ERR_UNSUPPORTED),
-    (dict(fixed_iters=5, guess=gcp.GUESSES["hpcp+"]), gcp.ERR_UNSUPPORTED),
-    (dict(fixed_iters=5, method=gcp.METHODS["pmcp"]), gcp.ERR_UNSUPPORTED),
+    (dict(fixed_iters=5, guess=3), gcp.ERR_INVALID_ARG),
+    (dict(fixed_iters=5, method=2), gcp.ERR_INVALID_ARG),
+    (dict(fixed_iters=5, method=gcp.METHODS["pmcp"], prec=gcp.PRECISIONS["fp32"]),
+     gcp.ERR_UNSUPPORTED),
 ])
 def test_backward_rejects(lib, handle, kw, expect):
     o = _opts(**kw)

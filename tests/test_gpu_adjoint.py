@@ -45,6 +45,43 @@ def test_adjoint_matches_oracle_reverse_mode(solver, M, N, K, ck):
     assert np.abs(gH - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("M,N,guess,method", [
+    (40, 10, "canonical", "pmcp"),  # c <= 1/2 branch of Eq. pm1
+    (40, 30, "canonical", "pmcp"),  # c > 1/2 branch
+    (45, 11, "hpcp+", "hpcp"),      # alpha an interior root of Eq. hpcpguessalpha
+    (45, 22, "hpcp+", "hpcp"),      # middle filling, alpha = 1/2
+    (45, 34, "hpcp+", "pmcp"),
+    (48, 24, "hole", "hpcp"),
+    (48, 24, "hole", "pmcp"),
+])
+def test_adjoint_guesses_and_pmcp_match_oracle(solver, M, N, guess, method):
+    H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.2), (0.2, 1.0), seed=M + N)
+    G = inputs.symmetric_gaussian(M, 0.3, seed=M + N + 1)
+    K = 12
+    ref, _ = o.reverse_mode_grad(H, N, K, G_D=G, g_E=1.0, guess=guess, method=method)
+    gH = solver.backward(_dev(H), N, K, G_D=_dev(G), g_E=1.0, ckpt_every=5, guess=guess,
+                         method=method).cpu().numpy()
+    assert np.abs(gH - gH.T).max() <= 1e-14 * max(1.0, np.abs(ref).max())
+    assert np.abs(gH - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
+    # the conserved trace
+    I = torch.eye(M, dtype=torch.float64, device="cuda")
+    gT = solver.backward(_dev(H), N, K, G_D=I, g_E=0.0, guess=guess, method=method)
+    assert float(gT.abs().max()) <= 1e-12
+
+
+def test_fp32_adjoint_hpcp_plus_guess(solver):
+    """The FP32 adjoint from the HPCP+ guess against the FP64 one."""
+    M, N, K = 300, 75, 25
+    H, _, _ = inputs.rotated_spectrum(M, N, (-1.0, -0.1), (0.1, 1.0), seed=91)
+    G = inputs.symmetric_gaussian(M, 0.3, seed=92)
+    H32, G32 = _dev(H).float(), _dev(G).float()
+    ref = solver.backward(H32.double(), N, K, G_D=G32.double(), g_E=1.0,
+                          guess="hpcp+").cpu().numpy()
+    g = solver.backward(H32, N, K, G_D=G32, g_E=1.0, prec="fp32",
+                        guess="hpcp+").double().cpu().numpy()
+    assert np.abs(g - ref).max() <= FP32_BAR * np.abs(ref).max()
+
+
 def test_adjoint_checkpoint_interval_does_not_matter(solver):
     M, N, K = 50, 12, 17
     H, _, _ = inputs.rotated_spectrum(M, N, seed=3)
