@@ -115,9 +115,9 @@ constexpr uint32_t kPartBytes = kABytes + kBBytes;  // 24 KB: the hi (or lo) par
 constexpr uint32_t kSmemBytes = (kLoSlots + kHiSlots) * kPartBytes + 1024;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kTmemCols = 512;  // two 256-column accumulator buffers
-// Scratch slot: a finished tile row-major (BM x BN) and transposed (BN x BM).
+// Scratch slot: a finished tile, row-major (BM x BN).
 constexpr size_t kTileFloats = (size_t)BM * BN;
-constexpr size_t kSlotFloats = 2 * kTileFloats;
+constexpr size_t kSlotFloats = kTileFloats;  // one row-major tile per scratch slot
 
 struct Epi {
   const float* X;    // current shifted iterate (FP32, Mp x Mp)
@@ -277,23 +277,53 @@ __device__ __forceinline__ void store_out1(const Epi& ep, size_t off, float o) {
 // The epilogues of the split GEMMs work on 32 x 32 blocks of the output with
 // eight lanes per row and four consecutive columns per lane, so every load
 // and store is a whole 128-byte row segment.  A block above the diagonal is
-// written twice: the direct pass (rows r, columns c) reads the product from
-// the row-major scratch tile, the mirror pass (rows c, columns r) from the
-// transposed copy the drain warps wrote.  The mirror pass recomputes each
-// value from the same inputs (X and Sigma are stored exactly symmetric), so
-// the two stores are bitwise equal, without a shared-memory transpose.  On a
-// diagonal block the direct pass keeps the elements on or above the
-// diagonal and the mirror pass those strictly below.
+// written twice: the direct pass (rows r, columns c) computes it from the
+// row-major scratch tile and stores it; each 16-row half of its values then
+// goes through a per-warp shared-memory buffer and is stored transposed
+// (rows c, columns r), so the mirror costs no loads.  On a diagonal block
+// the direct pass keeps the elements on or above the diagonal and the
+// mirror those strictly below.
+constexpr int kStageLd = 33;  // row stride of a warp's 16 x 32 staging buffer (floats)
+constexpr int kStageFloats = 16 * kStageLd;
 
-// GEMM1 epilogue of one warp for one 32 x 32 block: output rows orow0..,
-// columns ocol0..; `yb` points at s^2 (X X) for the block's first element in
-// the scratch tile, row stride ys.  Sigma = 2 theta X + Y and its halves are
-// stored; the direct pass (MIRROR false) also accumulates the partial sums.
-template <bool BF16, bool MIRROR>
+// Transposed store of the 16 x 32 values in `stage` (rows h16.. of the
+// direct block with first row orow0 and first column ocol0): output rows
+// ocol0 + c, columns orow0 + h16 + r; on a diagonal block only the elements
+// below the diagonal.  put4(off, float4) / put1(off, float) store.
+template <typename Put4, typename Put1>
+__device__ __forceinline__ void mirror_half(const float* __restrict__ stage, int Mp, int orow0,
+                                            int ocol0, int h16, bool diag_blk, Put4 put4,
+                                            Put1 put1) {
+  const int lane = threadIdx.x & 31;
+  const int mc = 4 * (lane & 3);
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int mr = (lane >> 2) + 8 * k;
+    const float4 o = make_float4(stage[(mc + 0) * kStageLd + mr], stage[(mc + 1) * kStageLd + mr],
+                                 stage[(mc + 2) * kStageLd + mr], stage[(mc + 3) * kStageLd + mr]);
+    const int R = ocol0 + mr, C = orow0 + h16 + mc;
+    const size_t off = (size_t)R * Mp + C;
+    if (!diag_blk) {
+      put4(off, o);
+    } else {
+      const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (C + q < R) put1(off + q, ov[q]);
+    }
+  }
+}
+
+// GEMM1 epilogue of one warp for one 32 x 32 block and its mirror: output
+// rows orow0.., columns ocol0..; `yb` points at s^2 (X X) for the block's
+// first element in the scratch tile, row stride ys.  Sigma = 2 theta X + Y
+// and its halves are stored, and the partial sums accumulated.
+template <bool BF16>
 __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restrict__ yb, int ys,
                                            int orow0, int ocol0, bool diag_blk, float thf,
                                            float f2th, float thtb, float (&pp)[3],
-                                           double (&dpart)[2]) {
+                                           double (&dpart)[2], float* __restrict__ stage) {
+  constexpr bool MIRROR = false;
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
@@ -318,6 +348,13 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
       o.y = fmaf(f2th, xx[j].y, yy[j].y * is2);
       o.z = fmaf(f2th, xx[j].z, yy[j].z * is2);
       o.w = fmaf(f2th, xx[j].w, yy[j].w * is2);
+      {
+        float* st = stage + (rs + 4 * j) * kStageLd + cl;
+        st[0] = o.x;
+        st[1] = o.y;
+        st[2] = o.z;
+        st[3] = o.w;
+      }
       if (!diag_blk) {
         if (!MIRROR) {
           // every element lies above the diagonal (weight 2: it stands for
@@ -363,6 +400,12 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
         }
       }
     }
+    // rows 4 jh .. 4 jh + 15 of the block, mirrored
+    __syncwarp();
+    mirror_half(stage, Mp, orow0, ocol0, 4 * jh, diag_blk,
+                [&](size_t off, float4 o) { store_out4<BF16>(ep, off, o); },
+                [&](size_t off, float v) { store_out1<BF16>(ep, off, v); });
+    __syncwarp();
   }
 }
 
@@ -370,10 +413,12 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
 // (`yb`: s^2 (X Sigma) in the scratch tile): X_{n+1} = ca X + cb Sigma +
 // cz Z (+ cj on the diagonal of the unpadded block).  Without products (mma
 // false) the block is a copy of X and `yb` is not read.
-template <bool BF16, bool MIRROR>
+template <bool BF16>
 __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restrict__ yb, int ys,
                                            int orow0, int ocol0, bool diag_blk, bool mma,
-                                           float ca, float cb, float cj, float cz) {
+                                           float ca, float cb, float cj, float cz,
+                                           float* __restrict__ stage) {
+  constexpr bool MIRROR = false;
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
@@ -404,6 +449,13 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
         o.z = fmaf(ca, xx[j].z, fmaf(cb, ss[j].z, cz * (yy[j].z * is2)));
         o.w = fmaf(ca, xx[j].w, fmaf(cb, ss[j].w, cz * (yy[j].w * is2)));
       }
+      {
+        float* st = stage + ((rs + 4 * (jh + j)) & 15) * kStageLd + cl;
+        st[0] = o.x;
+        st[1] = o.y;
+        st[2] = o.z;
+        st[3] = o.w;
+      }
       if (!diag_blk) {
         store_out4<BF16>(ep, off, o);
       } else {
@@ -417,15 +469,24 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
         }
       }
     }
+    if ((jh & 3) == 2) {
+      // rows 4 jh - 8 .. 4 jh + 7 of the block, mirrored
+      __syncwarp();
+      mirror_half(stage, Mp, orow0, ocol0, 4 * jh - 8, diag_blk,
+                  [&](size_t off, float4 o) { store_out4<BF16>(ep, off, o); },
+                  [&](size_t off, float v) { store_out1<BF16>(ep, off, v); });
+      __syncwarp();
+    }
   }
 }
 
 // Plain-product epilogue (modes 5 and 6) of one warp for one 32 x 32 block:
 // C = inv_s2 (A B) in FP32, laid out as gemm1_pass.  Mode 6 writes a block
-// above the diagonal twice (direct and mirror pass).
+// above the diagonal twice (direct and mirror, through `stage`).
 template <bool MIRROR>
 __device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restrict__ yb, int ys,
-                                           int orow0, int ocol0, bool diag_blk) {
+                                           int orow0, int ocol0, bool diag_blk,
+                                           float* __restrict__ stage) {
   const int lane = threadIdx.x & 31;
   const int rs = lane >> 3, cl = 4 * (lane & 7);
   const float sc = ep.inv_s2;
@@ -440,6 +501,13 @@ __device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restric
       const int r = orow0 + rs + 4 * (jh + j);
       const size_t off = (size_t)r * ep.Mp + ocol0 + cl;
       const float4 o = make_float4(yy[j].x * sc, yy[j].y * sc, yy[j].z * sc, yy[j].w * sc);
+      if (MIRROR) {
+        float* st = stage + (rs + 4 * j) * kStageLd + cl;
+        st[0] = o.x;
+        st[1] = o.y;
+        st[2] = o.z;
+        st[3] = o.w;
+      }
       if (!diag_blk) {
         *reinterpret_cast<float4*>(ep.out + off) = o;
       } else {
@@ -447,10 +515,17 @@ __device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restric
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int c = ocol0 + cl + i;
-          if (MIRROR ? (c >= r) : (c < r)) continue;
+          if (c < r) continue;
           ep.out[off + i] = ov[i];
         }
       }
+    }
+    if (MIRROR) {
+      __syncwarp();
+      mirror_half(stage, ep.Mp, orow0, ocol0, 4 * jh, diag_blk,
+                  [&](size_t off, float4 o) { *reinterpret_cast<float4*>(ep.out + off) = o; },
+                  [&](size_t off, float v) { ep.out[off] = v; });
+      __syncwarp();
     }
   }
 }
@@ -580,6 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t never_bar;      // no thread arrives on it (diagnostic)
   __shared__ uint32_t tmem_holder;
   __shared__ double red[2 * 4 * 5];
+  __shared__ float epi_stage[4 * kStageFloats];  // one 16 x 32 staging buffer per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -795,51 +871,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         alive = false;
         break;
       }
-      // row-major (a thread's 128 columns of its row) and transposed (for a
-      // column k the lanes write 32 consecutive rows: 128-byte segments)
+      // row-major: a thread's 128 columns of its row
       float* tile = slots + slot * kSlotFloats;
       float4* dst = reinterpret_cast<float4*>(tile + (size_t)(32 * q + lane) * BN + half * 128);
 #pragma unroll
       for (int k = 0; k < 32; ++k)
         __stcg(dst + k, make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]));
-      // transposed: the four lanes of a quad hold four consecutive rows; a
-      // 4 x 4 transpose across the quad (two xor-shuffle stages) gives lane
-      // 4 m + p column 4 j + p of those rows, stored as one float4
-      const int p4 = lane & 3;
-      float* tq = tile + kTileFloats + (size_t)(half * 128) * BM + 32 * q + (lane & ~3);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float v0 = acc[4 * j], v1 = acc[4 * j + 1], v2 = acc[4 * j + 2], v3 = acc[4 * j + 3];
-        // stage 1 (partner lane ^ 1): swap the off-diagonal 1 x 1 pairs
-        {
-          const bool odd = p4 & 1;
-          const float s0 = odd ? v0 : v1, s1 = odd ? v2 : v3;
-          const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-          const float r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-          if (odd) {
-            v0 = r0;
-            v2 = r1;
-          } else {
-            v1 = r0;
-            v3 = r1;
-          }
-        }
-        // stage 2 (partner lane ^ 2): swap the off-diagonal 2 x 2 blocks
-        {
-          const bool up = p4 & 2;
-          const float s0 = up ? v0 : v2, s1 = up ? v1 : v3;
-          const float r0 = __shfl_xor_sync(0xffffffffu, s0, 2);
-          const float r1 = __shfl_xor_sync(0xffffffffu, s1, 2);
-          if (up) {
-            v0 = r0;
-            v1 = r1;
-          } else {
-            v2 = r0;
-            v3 = r1;
-          }
-        }
-        __stcg(reinterpret_cast<float4*>(tq + (size_t)(4 * j + p4) * BM), make_float4(v0, v1, v2, v3));
-      }
       __threadfence_block();
       __syncwarp();
       if (lane == 0) mbar_arrive(&sfull_bar[slot]);
@@ -880,23 +917,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool dblk = MODE != 5 && jb == c.I && part == e;
           const int cl0 = half * 128 + part * 32;  // tile-local column of the block
           const int c0 = c.J * BN + cl0;
-          // direct: rows row0.., columns c0.. (row-major copy); mirror: rows
-          // c0.., columns row0.. (transposed copy)
+          // rows row0.., columns c0.. of the row-major scratch tile (and
+          // their mirror, through this warp's staging buffer)
           const float* yd = tile + (size_t)(32 * e) * BN + cl0;
-          const float* ym = tile + kTileFloats + (size_t)cl0 * BM + 32 * e;
+          float* stage = epi_stage + e * kStageFloats;
           if constexpr (MODE == 1) {
             const double th = c.ep.st->theta;
             const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
-            gemm1_pass<BF16, false>(c.ep, yd, BN, row0, c0, dblk, thf, f2th, thtb, pp, dpart);
-            gemm1_pass<BF16, true>(c.ep, ym, BM, c0, row0, dblk, thf, f2th, thtb, pp, dpart);
+            gemm1_pass<BF16>(c.ep, yd, BN, row0, c0, dblk, thf, f2th, thtb, pp, dpart, stage);
           } else if constexpr (MODE == 2) {
-            gemm2_pass<BF16, false>(c.ep, yd, BN, row0, c0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
-            gemm2_pass<BF16, true>(c.ep, ym, BM, c0, row0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz);
+            gemm2_pass<BF16>(c.ep, yd, BN, row0, c0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz, stage);
           } else if constexpr (MODE == 5) {
-            plain_pass<false>(c.ep, yd, BN, row0, c0, false);
+            plain_pass<false>(c.ep, yd, BN, row0, c0, false, stage);
           } else if constexpr (MODE == 6) {
-            plain_pass<false>(c.ep, yd, BN, row0, c0, dblk);
-            plain_pass<true>(c.ep, ym, BM, c0, row0, dblk);
+            plain_pass<true>(c.ep, yd, BN, row0, c0, dblk, stage);
           } else if constexpr (MODE == 4) {
             const float inv = (float)(1.0 / (kRefScale * check_delta_scale(c.ep.st->R)));
             check_seg(c.ep, row0 + lane, c0, jb == c.I, yd + lane * BN, inv, pp, dpart);
