@@ -8,13 +8,13 @@
 //     integers, exact in fp16.  M <= 16384: b = 6, ns = 8 (48-bit fixed
 //     point); larger M: b = 5, ns = 9 (45 bits);
 //   * (D D)_ij = 2^(e_i+e_j) sum_w B^-(w+2) sum_{s+t=w} sum_k d_s(i,k) d_t(j,k)
-//     over the weights w kept: w = 0..ns (b = 6: 43 pairs; b = 5: 53).  The
-//     dropped weights have random signs except on the diagonal, where the
-//     first dropped square d_5(i,k)^2 (weight 10) is always positive:
-//     dropping it would bias Tr D^2 (~ -5e-9 at M = 8192 for b = 5), so the
-//     pair (5, 5) is kept too.  What is left adds ~1e-14 per element at
-//     M = 8192.  (Keeping b = 6 weights only up to 7 saved 15% more time but
-//     moved Tr D of a tight-binding D by 3e-9);
+//     over the weights w kept: at most w = 0..ns (b = 6: 43 pairs; b = 5:
+//     53), fewer when the refinement's tolerance allows (oz_weight_cap).
+//     The dropped weights have random signs except on the diagonal, where
+//     the dropped squares d_s(i,k)^2 are always positive; the diagonal is
+//     therefore not taken from this product but formed in FP64 by the
+//     finalize pass (finalize_rows).  What is left adds ~1e-14 per element at
+//     M = 8192 with all weights;
 //   * a pass accumulates one weight over at most P pairs with
 //     P (B/2)^2 M <= 2^24, so every partial sum is an integer below 2^24 and
 //     the FP32 tensor-core accumulation is exact whatever its rounding mode
@@ -648,10 +648,11 @@ int oz_num_slices(int M) { return oz_digit_bits(M) == 6 ? 8 : 9; }
 // stayed 2-20x below it).  F is taken at the largest M of the digit base
 // (16384 for b = 6, 32768 for b = 5), so that W depends on tol alone and a
 // batch shares the plan of its single solves; W is the smallest weight with
-// F(W) <= tol / 8: tol = 1e-6 gives W = 6 (29 products instead of 44;
-// F = 1.1e-7), tol = 1e-7 W = 7 (37), tol <= 1e-8 all weights.  The diagonal of D^2, whose dropped squares do
-// not cancel, is formed exactly in FP64 whatever W (finalize_rows), so
-// Tr D^2 does not depend on it; the idempotency stop test compares the
+// F(W) <= tol / 8: tol = 1e-6 gives W = 6 (28 products instead of 43;
+// F = 1.1e-7), tol = 1e-7 W = 7 (36), tol <= 1e-8 all weights (43).  The
+// diagonal of D^2, whose dropped squares do not cancel, is formed exactly in
+// FP64 whatever W (finalize_rows), so Tr D^2 does not depend on it; the
+// idempotency stop test compares the
 // residual with tol - F(W) (oz_tail_estimate), so that the residual of the
 // exact square of the returned D stays below tol.
 namespace {
@@ -681,8 +682,7 @@ double oz_tail_estimate(int M, double tol) {
 namespace {
 // Passes for an M-long inner dimension: pairs (s, w - s) with
 // 0 <= s, w - s < ns for the kept weights w <= wcap (at most b = 6: 0..8;
-// b = 5: 0..9), at most floor(2^24 / ((B/2)^2 M)) pairs a pass, then the
-// first dropped square.
+// b = 5: 0..9), at most floor(2^24 / ((B/2)^2 M)) pairs a pass.
 int oz_plan(int M, int wcap, OzPlan* plan) {
   const int db = oz_digit_bits(M), nsl = oz_num_slices(M);
   const int wmax = (wcap > 0 && wcap < nsl) ? wcap : nsl;  // 8 (b = 6) or 9 (b = 5) at most
@@ -704,15 +704,6 @@ int oz_plan(int M, int wcap, OzPlan* plan) {
       lo += n;
     }
   }
-  // the first dropped square ((5, 5) of weight 10 for all weights; see the
-  // top of the file)
-  const int wsq = (wmax + 1) % 2 == 0 ? wmax + 1 : wmax + 2;
-  if (wsq / 2 >= nsl) return 0;
-  if (plan->npass >= kOzMaxPass) return 1;
-  plan->w[plan->npass] = wsq;
-  plan->s0[plan->npass] = wsq / 2;
-  plan->ns[plan->npass] = 1;
-  ++plan->npass;
   return 0;
 }
 }  // namespace

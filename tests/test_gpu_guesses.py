@@ -114,10 +114,15 @@ def test_pmcp_split_step(solver, prec, tol):
 
 
 def test_unsupported_combinations(solver):
+    """The FP64 adjoint differentiates PM steps; the FP32 one does not."""
     from paper_1512_07236_gb300 import gcp
     H, N, _, _ = _rot(64, 0.25, 0.2, 61)
+    out = torch.empty(64, 64, dtype=torch.float64, device="cuda")
     o_ = gcp.make_options(prec="fp64", fixed_iters=5, method="pmcp")
     st = solver.lib.gcp_backward(solver.h, _dev(H).data_ptr(), 64, N, 64, gcp.F64, None, 1.0,
-                                 torch.empty(64, 64, dtype=torch.float64, device="cuda").data_ptr(),
-                                 gcp.C.byref(o_))
+                                 out.data_ptr(), gcp.C.byref(o_))
+    assert st == gcp.OK
+    o_ = gcp.make_options(prec="fp32", fixed_iters=5, method="pmcp")
+    st = solver.lib.gcp_backward(solver.h, _dev(H).data_ptr(), 64, N, 64, gcp.F64, None, 1.0,
+                                 out.data_ptr(), gcp.C.byref(o_))
     assert st == gcp.ERR_UNSUPPORTED
