@@ -57,15 +57,16 @@
 // Schedule.  Persistent CTAs (one per SM) walk the 128 x 256 tiles of the
 // upper block triangle with four warpgroups of specialised warps:
 //   * warpgroup 0: warp 0 lane 0 issues the TMA loads (SWIZZLE_64B, 32-wide
-//     K blocks, a 4-stage ring of 48 KB stages, each in a hi and a lo half),
-//     warp 1 lane 0 the tcgen05.mma;
+//     K blocks; each stage's hi part and lo part, 24 KB each, in rings of 5
+//     and 4 slots), warp 1 lane 0 the tcgen05.mma;
 //   * warpgroups 1-2, eight drain warps: warp w reads TMEM lanes
 //     32 (w % 4).. and columns 128 ((w - 4) / 4).. of each chunk and keeps
 //     the tile's 128 x 256 FP32 sum in registers (128 a thread); at the end
 //     of a tile they store it to one of two scratch slots of this CTA in
 //     global memory (128 KB each, L2-resident) and start on the next tile;
 //   * warpgroup 3, four epilogue warps: the tile's epilogue from the scratch
-//     slot, rows 32 e.. for warp 12 + e, while the next tile accumulates.
+//     slot, rows 32 e.. for warp 12 + e, while the next tile accumulates;
+//     each warp mirrors its blocks through a 16 x 32 shared-memory buffer.
 // So the MMA warp never waits for an epilogue (it waited ~25 % of a tile at
 // M = 8192 when the drain warps also ran the epilogue).  Register budgets
 // (setmaxnreg): 40 / 176 / 120 a thread against 128 at launch.  Blocks
