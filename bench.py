@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=2)
     p.add_argument("--no-graph", action="store_true",
                    help="host-driven loop (same kernels, one launch each; for launch lists)")
-    p.add_argument("--workload", default="dense", choices=["dense", "tb", "batched", "adjoint"],
+    p.add_argument("--workload", default="dense",
+                   choices=["dense", "tb", "batched", "adjoint", "pbar"],
                    help="dense: the headline (one dense H); tb: tight-binding 20^3 insulator; "
                         "batched: 512 uneven instances; adjoint: dL/dH through 40 steps")
     return p.parse_args()
@@ -304,6 +305,18 @@ def run_workload(args, rank):
                 single.solve(H, N, **opts)
             loop_ms, _ = _cuda_ms(lambda: [single.solve(H, N, **opts) for H, N in zip(Hs, Ns)],
                                   1, stream)
+        # the same batch split by size class, each class timed on its own
+        # (small instances are bound by per-tile latency, not by the MMAs)
+        buckets = {}
+        for lo, hi in ((64, 256), (257, 512), (513, 768), (769, 1024)):
+            idx = [k for k, H in enumerate(Hs) if lo <= H.shape[0] <= hi]
+            if not idx:
+                continue
+            Hb, Nb = [Hs[k] for k in idx], [Ns[k] for k in idx]
+            solver.solve_batched(Hb, Nb, **opts)
+            bms, _ = _cuda_ms(lambda: solver.solve_batched(Hb, Nb, **opts), 1, stream)
+            buckets[f"M {lo}-{hi}"] = {"instances": len(idx), "solves_per_s": len(idx) / (bms * 1e-3),
+                                       "ms": bms}
         errs = []
         for (H, N, eps, Q), Dk in zip(items[:32], Ds[:32]):
             Qo = torch.from_numpy(Q[:, :N]).cuda()
@@ -319,8 +332,49 @@ def run_workload(args, rank):
             "loop_of_single_solves_per_s": 512 / (loop_ms * 1e-3) if loop_ms else None,
             "speedup_vs_loop": loop_ms / ms if loop_ms else None,
             "effective_tflops": flops / (ms * 1e-3) / 1e12,
+            "by_size": buckets,
             "status_ok": sum(1 for i in infos if i["status"] == 0),
             "max_subspace_err_first32": max(errs), "clocks": clk.summary()})
+    elif args.workload == "pbar":
+        # Fig. 3: mean iteration counts on the paper's diagonal M = 100 test
+        # matrices, 32 per point, stop at Tr(D Dbar) <= 1e-6, one batched FP64
+        # solve per point (HPCP / PMCP steps, canonical / HPCP+ guess)
+        Mq, per = 100, 32
+        thetas, gaps = (0.05, 0.1, 0.2, 0.3, 0.4, 0.5), (1.0, 1e-2, 1e-4)
+        variants = (("hpcp", "canonical"), ("pmcp", "canonical"), ("hpcp", "hpcp+"))
+        batches = []
+        for th in thetas:
+            for g in gaps:
+                Nq = int(round(th * Mq))
+                Hs = [torch.from_numpy(inputs.diagonal_spectrum(Mq, Nq, g, seed=1000 + k)[0]).cuda()
+                      for k in range(per)]
+                batches.append((th, g, Nq, Hs))
+        table = []
+
+        def run_all():
+            out = []
+            for th, g, Nq, Hs in batches:
+                row = {"theta": th, "gap": g}
+                for meth, gs in variants:
+                    _, infos = solver.solve_batched(Hs, [Nq] * per, prec="fp64", stop="trace",
+                                                    tol=1e-6, method=meth, guess=gs)
+                    row[f"{meth}/{gs}"] = float(np.mean([i["iters"] for i in infos]))
+                out.append(row)
+            return out
+
+        for _ in range(W):
+            run_all()
+        with ClockSampler(0) as clk:
+            ms, table = _cuda_ms(run_all, K, stream)
+        nsolve = len(batches) * per * len(variants)
+        line.update({
+            "metric": "p-bar study: batched FP64 solves/s (Fig. 3 matrices)",
+            "value": nsolve / (ms * 1e-3), "unit": "solves/s", "higher_is_better": True,
+            "ms_per_step": ms, "dtype": "f64",
+            "config": {"workload": "diagonal M=100, eigenvalues in [-2.5, eps_N] u [eps_N+1, 2.5], "
+                                   "32 per point, stop Tr(D Dbar) <= 1e-6",
+                       "thetas": list(thetas), "gaps": list(gaps)},
+            "pbar": table, "clocks": clk.summary()})
     else:  # adjoint
         M, N, Kst = 2048, 512, 40
         H, eps, Q = inputs.rotated_spectrum(M, N, (-1.0, -0.025), (0.025, 1.0), seed=5,
