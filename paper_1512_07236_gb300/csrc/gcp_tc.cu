@@ -324,7 +324,6 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
                                            int orow0, int ocol0, bool diag_blk, float thf,
                                            float f2th, float thtb, float (&pp)[3],
                                            double (&dpart)[2], float* __restrict__ stage) {
-  constexpr bool MIRROR = false;
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
@@ -357,14 +356,12 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
         st[3] = o.w;
       }
       if (!diag_blk) {
-        if (!MIRROR) {
-          // every element lies above the diagonal (weight 2: it stands for
-          // its mirror too)
-          const float ex = o.x - xx[j].x, ey = o.y - xx[j].y, ez = o.z - xx[j].z,
-                      ew = o.w - xx[j].w;
-          pp[0] += 2.f * (o.x * xx[j].x + o.y * xx[j].y + o.z * xx[j].z + o.w * xx[j].w);
-          pp[1] += 2.f * (ex * ex + ey * ey + ez * ez + ew * ew);
-        }
+        // every element lies above the diagonal (weight 2: it stands for
+        // its mirror too)
+        const float ex = o.x - xx[j].x, ey = o.y - xx[j].y, ez = o.z - xx[j].z,
+                    ew = o.w - xx[j].w;
+        pp[0] += 2.f * (o.x * xx[j].x + o.y * xx[j].y + o.z * xx[j].z + o.w * xx[j].w);
+        pp[1] += 2.f * (ex * ex + ey * ey + ez * ez + ew * ew);
         store_out4<BF16>(ep, off, o);
       } else {
         const float xs[4] = {xx[j].x, xx[j].y, xx[j].z, xx[j].w};
@@ -372,22 +369,20 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int c = ocol0 + cl + i;
-          if (MIRROR ? (c >= r) : (c < r)) continue;
-          if (!MIRROR) {
-            const bool on_diag = c == r && r < ep.M;
-            const float w = c == r ? 1.f : 2.f;
-            const float e = os[i] - xs[i] - (on_diag ? thtb : 0.f);  // (S - D)_rc
-            pp[0] += w * os[i] * xs[i];
-            pp[1] += w * e * e;
-            if (on_diag) {
-              dpart[0] += (double)xs[i];
-              dpart[1] += (double)os[i];
-            }
+          if (c < r) continue;
+          const bool on_diag = c == r && r < ep.M;
+          const float w = c == r ? 1.f : 2.f;
+          const float e = os[i] - xs[i] - (on_diag ? thtb : 0.f);  // (S - D)_rc
+          pp[0] += w * os[i] * xs[i];
+          pp[1] += w * e * e;
+          if (on_diag) {
+            dpart[0] += (double)xs[i];
+            dpart[1] += (double)os[i];
           }
           store_out1<BF16>(ep, off + i, os[i]);
         }
       }
-      if (!MIRROR && ep.H) {
+      if (ep.H) {
         const float xs[4] = {xx[j].x, xx[j].y, xx[j].z, xx[j].w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -419,7 +414,6 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
                                            int orow0, int ocol0, bool diag_blk, bool mma,
                                            float ca, float cb, float cj, float cz,
                                            float* __restrict__ stage) {
-  constexpr bool MIRROR = false;
   const int lane = threadIdx.x & 31;
   const int Mp = ep.Mp;
   const float is2 = ep.inv_s2;
@@ -464,8 +458,8 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int c = ocol0 + cl + i;
-          if (MIRROR ? (c >= r) : (c < r)) continue;
-          const float v = (!MIRROR && mma && c == r && r < ep.M) ? ov[i] + cj : ov[i];
+          if (c < r) continue;
+          const float v = (mma && c == r && r < ep.M) ? ov[i] + cj : ov[i];
           store_out1<BF16>(ep, off + i, v);
         }
       }
