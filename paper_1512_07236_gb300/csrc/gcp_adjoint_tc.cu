@@ -63,8 +63,12 @@ __global__ void absmax_kernel(const float* __restrict__ A, size_t n,
 }
 
 // hi/lo fp16 halves of scale * A (scale a power of two: exact).
+// hi/lo fp16 halves of scale * A (scale a power of two: exact); the scale
+// from `sptr` when given (a device value, see scale_kernel).
 __global__ void split_kernel(const float* __restrict__ A, __half* __restrict__ h,
-                             __half* __restrict__ l, size_t n, float scale) {
+                             __half* __restrict__ l, size_t n, float scale,
+                             const float* __restrict__ sptr) {
+  if (sptr) scale = *sptr;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
     __half hh, ll;
@@ -74,14 +78,31 @@ __global__ void split_kernel(const float* __restrict__ A, __half* __restrict__ h
   }
 }
 
-// PT = P1^T + theta G (32 x 32 tiles through shared memory).
+// The power of two s = 2^(14 - e) with max |A| < 2^e (amax: the bit pattern
+// of max |A|) and 1 / (s xscale), the inverse scale of a product of the
+// halves of s A with those of xscale X, into out[0], out[1].
+__global__ void scale_kernel(const unsigned int* __restrict__ amax, float xscale,
+                             float* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  const float m = __uint_as_float(*amax);
+  int e = 0;
+  frexpf(m > 0.f ? m : 1.f, &e);  // m < 2^e
+  const float sc = ldexpf(1.f, 14 - e);
+  out[0] = sc;
+  out[1] = 1.f / (sc * xscale);
+}
+
+// PT = inv P1^T + theta G (32 x 32 tiles through shared memory); P1 is the
+// product of the halves, inv (device) its inverse scale.
 __global__ void __launch_bounds__(1024) transpose_add_kernel(const float* __restrict__ P1,
                                                              const float* __restrict__ G,
                                                              float* __restrict__ PT, int Mp,
-                                                             float theta) {
+                                                             float theta,
+                                                             const float* __restrict__ inv) {
   __shared__ float t[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  t[threadIdx.y][threadIdx.x] = P1[(size_t)(by + threadIdx.y) * Mp + bx + threadIdx.x];
+  const float sc = *inv;
+  t[threadIdx.y][threadIdx.x] = P1[(size_t)(by + threadIdx.y) * Mp + bx + threadIdx.x] * sc;
   __syncthreads();
   const int i = bx + threadIdx.y, j = by + threadIdx.x;
   PT[(size_t)i * Mp + j] = t[threadIdx.x][threadIdx.y] + theta * G[(size_t)i * Mp + j];
@@ -140,15 +161,17 @@ __global__ void __launch_bounds__(1024) combine_kernel(
     const float* __restrict__ G, const float* __restrict__ P1, const float* __restrict__ PT,
     const float* __restrict__ Q1, const float* __restrict__ R1, const float* __restrict__ X,
     const float* __restrict__ Sig, float* __restrict__ Gn, int M, int Mp, double cg, double cp,
-    double theta, double c, int restoring, double den_min, const double* __restrict__ sdm) {
+    double theta, double c, int restoring, double den_min, const double* __restrict__ sdm,
+    const float* __restrict__ inv_g, const float* __restrict__ inv_r) {
   __shared__ float Qt[32][33];
   __shared__ float Rt[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const float sg = *inv_g, sr = *inv_r;  // inverse scales of P1, Q1 and of R1
   {
     const size_t o = (size_t)(bx + ty) * Mp + by + tx;
-    Qt[ty][tx] = Q1[o];
-    Rt[ty][tx] = R1[o];
+    Qt[ty][tx] = Q1[o] * sg;
+    Rt[ty][tx] = R1[o] * sr;
   }
   __syncthreads();
   const int i = by + ty, j = bx + tx;
@@ -163,9 +186,9 @@ __global__ void __launch_bounds__(1024) combine_kernel(
   const double d = (double)X[o] + theta * J;
   const double sv = (double)Sig[o] + theta * theta * J;
   const double dc = s != 0.0 ? ((2.0 * d - 3.0 * sv) + 0.5 * J - c * (J - 2.0 * d)) / den : 0.0;
-  const double v = cg * (double)G[o] + cp * ((double)P1[o] + (double)PT[o]) -
-                   2.0 * ((double)Q1[o] + (double)Qt[tx][ty]) - ((double)R1[o] + (double)Rt[tx][ty]) +
-                   s * dc;
+  const double v = cg * (double)G[o] + cp * ((double)(P1[o] * sg) + (double)PT[o]) -
+                   2.0 * ((double)(Q1[o] * sg) + (double)Qt[tx][ty]) -
+                   ((double)(R1[o] * sr) + (double)Rt[tx][ty]) + s * dc;
   Gn[o] = (float)v;
 }
 
@@ -214,14 +237,18 @@ struct AdjTcWs {
   double* G64 = nullptr;  // dL/dD_0 for the guess adjoint (M x M)
   double* DK = nullptr;   // D_K (M x M)
   double* red = nullptr;  // reduction partials and scalars
-  unsigned int* amax = nullptr;
+  unsigned int* amax = nullptr;  // [0]: max |G| bits, [1]: max |PT| bits
+  float* scal = nullptr;         // [0] s_G, [1] 1/(s_G 2^14), [2] s_PT, [3] 1/(s_PT 2^14)
   int* kinds = nullptr;  // per-step kStep* of the forward (kcap entries)
+  State* rst = nullptr;  // per-step replay states (kcap entries)
   int kcap = 0;
 };
 
 void free_ws(AdjTcWs* w) {
   if (w->kinds) cudaFree(w->kinds);
+  if (w->rst) cudaFree(w->rst);
   w->kinds = nullptr;
+  w->rst = nullptr;
   w->kcap = 0;
   for (void* p : w->bufs) cudaFree(p);
   w->bufs.clear();
@@ -317,8 +344,9 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
       w->DK = (double*)al(m2 * 8);
       w->red = (double*)al((2 * kRed + 64) * 8);
       w->amax = (unsigned int*)al(64);
+      w->scal = (float*)al(64);
       ok = w->ckX && w->G && w->Gn && w->P1 && w->Q1 && w->R1 && w->PT && w->Gh && w->Gl &&
-           w->PTh && w->PTl && w->G64 && w->DK && w->red && w->amax;
+           w->PTh && w->PTl && w->G64 && w->DK && w->red && w->amax && w->scal;
     }
     if (!ok) {
       free_ws(w);
@@ -335,9 +363,12 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
 
   if (w->kcap < K) {
     if (w->kinds) cudaFree(w->kinds);
+    if (w->rst) cudaFree(w->rst);
     w->kinds = nullptr;
+    w->rst = nullptr;
     w->kcap = 0;
     AT_CK(cudaMalloc((void**)&w->kinds, (size_t)K * sizeof(int)));
+    AT_CK(cudaMalloc((void**)&w->rst, (size_t)K * sizeof(State)));
     w->kcap = K;
   }
 
@@ -417,31 +448,24 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
   else
     gtc_init_kernel<float><<<rgrid(Mp, Mp), 256, 0, s>>>((const float*)GD, (const float*)H, ld,
                                                          gE, M, Mp, w->G);
-  State rs;  // replay state for the recomputation
-  memset(&rs, 0, sizeof rs);
-  rs.theta = theta;
-  // Every upload of the replay state overwrites the timeout flag the
-  // kernels before it may have raised: read it back first (the stream is
-  // synchronised there anyway, the host variable being reused).
-  auto timed_out = [&]() -> int {
-    State ts;
-    if (cudaMemcpyAsync(&ts, st, sizeof ts, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return -1;
-    return ts.timeout ? 1 : 0;
-  };
-#define AT_TIMEOUT()                                                                   \
-  do {                                                                                 \
-    const int t_ = timed_out();                                                        \
-    if (t_ < 0) {                                                                      \
-      snprintf(err, errlen, "gcp_backward (FP32): %s", cudaGetErrorString(cudaGetLastError())); \
-      return GCP_ERR_CUDA;                                                             \
-    }                                                                                  \
-    if (t_ > 0) {                                                                      \
-      snprintf(err, errlen, "gcp_backward (FP32): a device-side wait gave up");        \
-      return GCP_ERR_TIMEOUT;                                                          \
-    }                                                                                  \
-  } while (0)
+  // One replay state per step, uploaded once: the recomputed steps read
+  // their coefficients from it, and every kernel of step n that may raise a
+  // timeout writes it there, so the backward pass needs no host round trip
+  // until its end.
+  std::vector<State> rs((size_t)K);
+  for (int n = 0; n < K; ++n) {
+    State& r = rs[(size_t)n];
+    memset(&r, 0, sizeof r);
+    const double c = rec[(size_t)n * GCP_HISTORY_FIELDS + 5];
+    const bool applied = kind[n] != kStepIdentity;
+    r.theta = theta;
+    r.apply = applied ? 1 : 0;
+    r.a = applied ? 1.0 - 2.0 * c : 1.0;
+    r.b = applied ? 2.0 + 2.0 * c : 0.0;
+    r.g3 = -2.0;  // HPCP (Eq. hpcp3)
+    r.xshift = applied ? 2.0 * theta * (1.0 - theta) * (theta - c) : 0.0;
+  }
+  AT_CK(cudaMemcpyAsync(w->rst, rs.data(), (size_t)K * sizeof(State), cudaMemcpyHostToDevice, s));
   const dim3 tg(Mp / 32, Mp / 32), tb(32, 32);
   // the forward's 0/0 guard of the split phase
   const double den_min = 16.0 * sqrt((double)M) * kU32;
@@ -449,35 +473,24 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
   for (int seg = (K - 1) / ck; seg >= 0; --seg) {
     const int n0 = seg * ck, n1 = (n0 + ck < K) ? n0 + ck : K;
     AT_CK(cudaMemcpyAsync(w->X[0], w->ckX + (size_t)seg * n2, n2 * 4, cudaMemcpyDeviceToDevice, s));
-    split_kernel<<<eb, 256, 0, s>>>(w->X[0], (__half*)w->Xh[0], (__half*)w->Xl[0], n2, kXScale);
+    split_kernel<<<eb, 256, 0, s>>>(w->X[0], (__half*)w->Xh[0], (__half*)w->Xl[0], n2, kXScale,
+                                    nullptr);
     for (int n = n0; n < n1; ++n) {
       const int j = n - n0;
-      const double c = rec[(size_t)n * GCP_HISTORY_FIELDS + 5];
-      const bool applied = kind[n] != kStepIdentity;
-      rs.stopped = 0;
-      rs.apply = applied ? 1 : 0;
-      rs.a = applied ? 1.0 - 2.0 * c : 1.0;
-      rs.b = applied ? 2.0 + 2.0 * c : 0.0;
-      rs.g3 = -2.0;  // HPCP (Eq. hpcp3)
-      rs.xshift = applied ? 2.0 * theta * (1.0 - theta) * (theta - c) : 0.0;
-      AT_TIMEOUT();
-      AT_CK(cudaMemcpyAsync(st, &rs, sizeof rs, cudaMemcpyHostToDevice, s));
+      State* sn = w->rst + n;
       if (tc_launch_gemm1(w->opX[j], w->X[j], w->S[j], w->Sh[j], w->Sl[j], M, Mp, nullptr, 1, M,
-                          part, st, 0, kXScale, scratch, s) ||
+                          part, sn, 0, kXScale, scratch, s) ||
           (n + 1 < n1 && tc_launch_gemm2(w->opS[j], w->opX[j], w->X[j], w->S[j], w->X[j + 1],
-                                         w->Xh[j + 1], w->Xl[j + 1], M, Mp, st, 0, kXScale,
+                                         w->Xh[j + 1], w->Xl[j + 1], M, Mp, sn, 0, kXScale,
                                          scratch, s))) {
         snprintf(err, errlen, "gcp_backward (FP32): recompute launch failed: %s",
                  cudaGetErrorString(cudaGetLastError()));
         return GCP_ERR_CUDA;
       }
     }
-    // the products below read st (stopped = 0) for their timeout flag
-    rs.apply = 0;
-    AT_TIMEOUT();
-    AT_CK(cudaMemcpyAsync(st, &rs, sizeof rs, cudaMemcpyHostToDevice, s));
     for (int n = n1 - 1; n >= n0; --n) {
       const int j = n - n0;
+      State* sn = w->rst + n;
       const double* Rc = rec.data() + (size_t)n * GCP_HISTORY_FIELDS;
       const double c = Rc[5];
       if (kind[n] == kStepIdentity) continue;  // G passes through
@@ -488,38 +501,25 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
                                                theta * theta - theta, w->red);
         sum_finalize_kernel<<<1, 32, 0, s>>>(w->red, kRed, w->red + 2 * kRed);
       }
-      // halves of G at a power-of-two scale that keeps max |scale G| < 2^14
-      AT_CK(cudaMemsetAsync(w->amax, 0, 4, s));
+      // halves of G and of PT at power-of-two scales that keep their
+      // entries below 2^14 (scale_kernel); the products are stored unscaled
+      // and the kernels that read them apply the inverse scales
+      AT_CK(cudaMemsetAsync(w->amax, 0, 8, s));
       absmax_kernel<<<eb, 256, 0, s>>>(w->G, n2, w->amax);
-      unsigned int gbits = 0;
-      AT_CK(cudaMemcpyAsync(&gbits, w->amax, 4, cudaMemcpyDeviceToHost, s));
-      AT_CK(cudaStreamSynchronize(s));
-      float gmax;
-      memcpy(&gmax, &gbits, 4);
-      int eg = 0;
-      frexpf(gmax > 0.f ? gmax : 1.f, &eg);  // gmax < 2^eg
-      const float sg = ldexpf(1.f, 14 - eg);
-      split_kernel<<<eb, 256, 0, s>>>(w->G, (__half*)w->Gh, (__half*)w->Gl, n2, sg);
-      const float inv_gx = 1.f / (sg * kXScale);
-      if (tc_launch_product(w->opG, w->opX[j], w->P1, Mp, 0, inv_gx, st, scratch, s) ||
-          tc_launch_product(w->opG, w->opS[j], w->Q1, Mp, 0, inv_gx, st, scratch, s)) {
+      scale_kernel<<<1, 32, 0, s>>>(w->amax, kXScale, w->scal);
+      split_kernel<<<eb, 256, 0, s>>>(w->G, (__half*)w->Gh, (__half*)w->Gl, n2, 1.f, w->scal);
+      if (tc_launch_product(w->opG, w->opX[j], w->P1, Mp, 0, 1.f, sn, scratch, s) ||
+          tc_launch_product(w->opG, w->opS[j], w->Q1, Mp, 0, 1.f, sn, scratch, s)) {
         snprintf(err, errlen, "gcp_backward (FP32): product launch failed: %s",
                  cudaGetErrorString(cudaGetLastError()));
         return GCP_ERR_CUDA;
       }
-      transpose_add_kernel<<<tg, tb, 0, s>>>(w->P1, w->G, w->PT, Mp, (float)theta);
-      AT_CK(cudaMemsetAsync(w->amax, 0, 4, s));
-      absmax_kernel<<<eb, 256, 0, s>>>(w->PT, n2, w->amax);
-      AT_CK(cudaMemcpyAsync(&gbits, w->amax, 4, cudaMemcpyDeviceToHost, s));
-      AT_CK(cudaStreamSynchronize(s));
-      float pmax;
-      memcpy(&pmax, &gbits, 4);
-      int ep = 0;
-      frexpf(pmax > 0.f ? pmax : 1.f, &ep);
-      const float sp = ldexpf(1.f, 14 - ep);
-      split_kernel<<<eb, 256, 0, s>>>(w->PT, (__half*)w->PTh, (__half*)w->PTl, n2, sp);
-      if (tc_launch_product(w->opX[j], w->opPT, w->R1, Mp, 0, 1.f / (kXScale * sp), st, scratch,
-                            s)) {
+      transpose_add_kernel<<<tg, tb, 0, s>>>(w->P1, w->G, w->PT, Mp, (float)theta, w->scal + 1);
+      absmax_kernel<<<eb, 256, 0, s>>>(w->PT, n2, w->amax + 1);
+      scale_kernel<<<1, 32, 0, s>>>(w->amax + 1, kXScale, w->scal + 2);
+      split_kernel<<<eb, 256, 0, s>>>(w->PT, (__half*)w->PTh, (__half*)w->PTl, n2, 1.f,
+                                      w->scal + 2);
+      if (tc_launch_product(w->opX[j], w->opPT, w->R1, Mp, 0, 1.f, sn, scratch, s)) {
         snprintf(err, errlen, "gcp_backward (FP32): product launch failed: %s",
                  cudaGetErrorString(cudaGetLastError()));
         return GCP_ERR_CUDA;
@@ -527,20 +527,26 @@ int adjoint_backward_tc(void** wsp, const void* H, int M, int N, int ld, int h_f
       combine_kernel<<<tg, tb, 0, s>>>(w->G, w->P1, w->PT, w->Q1, w->R1, w->X[j], w->S[j], w->Gn,
                                        M, Mp, a + b * theta - 5.0 * theta * theta, b - theta,
                                        theta, c, kind[n] == kStepRestoring ? 1 : 0, den_min,
-                                       w->red + 2 * kRed);
+                                       w->red + 2 * kRed, w->scal + 1, w->scal + 3);
       AT_CK(cudaPeekAtLastError());
       float* t = w->G;
       w->G = w->Gn;
       w->Gn = t;
     }
   }
-  AT_TIMEOUT();
+  // any wait of the recomputation or of the products that gave up
+  AT_CK(cudaMemcpyAsync(rs.data(), w->rst, (size_t)K * sizeof(State), cudaMemcpyDeviceToHost, s));
+  AT_CK(cudaStreamSynchronize(s));
+  for (int n = 0; n < K; ++n)
+    if (rs[(size_t)n].timeout) {
+      snprintf(err, errlen, "gcp_backward (FP32): a device-side wait gave up");
+      return GCP_ERR_TIMEOUT;
+    }
   // ---------------- guess (FP64, shared with gcp_adjoint.cu) ---------------
   to_f64_kernel<<<rgrid(M, M), 256, 0, s>>>(w->G, Mp, M, w->G64);
   AT_CK(cudaPeekAtLastError());
   return adjoint_guess(H, M, N, ld, h_f64, guess, w->G64, w->DK, gE, dLdH, gpart, st, s, err,
                        errlen);
-#undef AT_TIMEOUT
 #undef AT_CK
 }
 
