@@ -298,6 +298,8 @@ def run_workload(args, rank):
             solver.solve_batched(Hs, Ns, **opts)
         with ClockSampler(0) as clk:
             ms, (Ds, infos) = _cuda_ms(lambda: solver.solve_batched(Hs, Ns, **opts), K, stream)
+        # work order of the tensor-core tiles, timed at the first solve
+        order_choice, order_ms = solver.batched_order()
         loop_ms = None
         if not args.skip_loop:
             single = gcp.Solver()
@@ -333,6 +335,9 @@ def run_workload(args, rank):
             "speedup_vs_loop": loop_ms / ms if loop_ms else None,
             "effective_tflops": flops / (ms * 1e-3) / 1e12,
             "by_size": buckets,
+            "work_order": {"choice": ["instance-major", "cost-sorted", "cost-sorted snake"][order_choice],
+                           "gemm1_ms": {"instance-major": order_ms[0], "cost-sorted": order_ms[1],
+                                        "cost-sorted snake": order_ms[2]}},
             "status_ok": sum(1 for i in infos if i["status"] == 0),
             "max_subspace_err_first32": max(errs), "clocks": clk.summary()})
     elif args.workload == "pbar":

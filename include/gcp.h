@@ -245,6 +245,25 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
                              const int* N, const int* ld, int h_dtype, void* const* D_out,
                              int d_dtype, gcp_result* res, const gcp_options* opt);
 
+/* Work order of the batched tensor-core products (scheduling only, no
+ * counterpart in the paper).  In split-precision batched solves the CTAs
+ * take the tiles of all instances' products from one work list; the first
+ * solve for a given set of instance sizes (with at least two tiles per SM)
+ * times the first step's GEMM1 under three candidate orders and keeps the
+ * fastest for later solves of those sizes on this handle: 0 = instance after
+ * instance, 1 = tiles by estimated cost, largest first, dealt to the CTAs in
+ * turn, 2 = as 1 with every other round dealt in reverse.  Results are the
+ * same under every order, bit for bit.
+ *
+ * gcp_set_batched_order: order = -1 (default) times the candidates; 0, 1
+ * or 2 fixes that candidate without timing.  GCP_ERR_INVALID_ARG otherwise.
+ * gcp_batched_order: *choice = the order the last split-precision batched
+ * solve used; ms (3 doubles, may be NULL) = the GEMM1 time of each
+ * candidate in milliseconds, -1 where none was timed (fewer tiles, or a
+ * fixed order).  Host-only; no device work. */
+gcp_status gcp_set_batched_order(void* handle, int order);
+gcp_status gcp_batched_order(void* handle, int* choice, double* ms);
+
 /* Reverse-mode derivative of L = <G_D, D_K> + g_E * Tr(H D_K), where D_K is
  * the iterate after exactly opt->fixed_iters steps of Eq. hpcp3 from the
  * guess of H (Eq. dmguess, Eq. pmcpguess); c_n depends on D_n (Eq. mcwgamb)

@@ -15,6 +15,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -67,6 +68,13 @@ struct Handle {
   std::vector<char> bkey;
   cudaGraph_t bgraph = nullptr;
   cudaGraphExec_t bexec = nullptr;
+  // the batched tensor-core work order chosen by timing: the instance sizes
+  // it was chosen for (with the half type), the candidate taken and the
+  // GEMM1 times measured (ms; -1 where not timed)
+  std::vector<int> tune_key;
+  int tune_force = -1;  // gcp_set_batched_order: a fixed candidate, or -1
+  int tune_choice = 0;
+  double tune_ms[3] = {-1.0, -1.0, -1.0};
   // adjoint workspaces (checkpoints, segment iterates, adjoint buffers):
   // FP64 and FP32 (tensor-core) forms
   void* adj = nullptr;
@@ -932,6 +940,8 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   off += al(sizeof(int) * (size_t)(ntc > 0 ? ntc : 1));
   const size_t tinst_f64_off = off;
   off += al(sizeof(int) * (size_t)(nf64 > 0 ? nf64 : 1));
+  const size_t order_off = off;
+  off += al(sizeof(int) * (size_t)(ntc > 0 ? ntc : 1));
   const size_t part_off = off;
   off += al(sizeof(double) * kPartFields * (size_t)nslots);
   const size_t gpart_off = off;
@@ -956,6 +966,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   BatchItem* items_d = (BatchItem*)(A + items_off);
   int* tinst_tc = (int*)(A + tinst_tc_off);
   int* tinst_f64 = (int*)(A + tinst_f64_off);
+  int* order_d = (int*)(A + order_off);
   double* part = (double*)(A + part_off);
   double* gpart = (double*)(A + gpart_off);
   int* active = (int*)(A + active_off);
@@ -1056,6 +1067,90 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
     CK(cudaMemcpy(tinst_f64, tf.data(), sizeof(int) * tf.size(), cudaMemcpyHostToDevice));
   }
 
+  // Order in which the CTAs take the tensor-core tiles, chosen once per set
+  // of instance sizes by timing GEMM1 of the first step (after the guess)
+  // with each candidate: (0) the work list's own order, instance after
+  // instance; (1) the tiles by estimated cost (tc_tile_cost), largest first,
+  // dealt to the CTAs in turn; (2) the same, each round of one tile per CTA
+  // dealt in the reverse direction of the one before.  A tile's arithmetic
+  // and its partials' place do not depend on the CTA that runs it, so the
+  // results are the same under every order.
+  const int* order = nullptr;
+  if (split && ntc > 0) {
+    std::vector<int> tk;
+    tk.reserve(nb + 2);
+    tk.push_back(h->tune_force);
+    tk.push_back(bf16);
+    for (int k = 0; k < nb; ++k) tk.push_back(items[k].Mp);
+    const bool retune = tk != h->tune_key;
+    if (fresh || retune) {
+      int dev = 0, nsm = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      const int G = ntc < nsm ? ntc : nsm;  // CTAs of a launch
+      std::vector<int> cost(ntc), lpt(ntc), snake(ntc);
+      for (int k = 0; k < nb; ++k)
+        for (int t = 0; t < items[k].tc_n; ++t)
+          cost[items[k].tc_off + t] = tc_tile_cost(items[k].Mp, t);
+      for (int t = 0; t < ntc; ++t) lpt[t] = t;
+      std::stable_sort(lpt.begin(), lpt.end(),
+                       [&cost](int a, int b) { return cost[a] > cost[b]; });
+      for (int t = 0; t < ntc; ++t) {
+        const int round = t / G, pos = t % G, r0 = round * G;
+        const int width = ntc - r0 < G ? ntc - r0 : G;
+        snake[t] = (round & 1) ? lpt[r0 + width - 1 - pos] : lpt[t];
+      }
+      const std::vector<int>* cand[3] = {nullptr, &lpt, &snake};
+      if (retune) {
+        int choice = 0;
+        double ms[3] = {-1.0, -1.0, -1.0};
+        if (h->tune_force >= 0) {
+          choice = h->tune_force;
+        } else if (ntc >= 2 * G) {
+          // the first step's state: guess and state set-up as the solve
+          // does them (the solve repeats both)
+          launch_batch_guess(items_d, nb, maxM, h64, 1, bf16, kSplitScale, gpart, gstride,
+                             o.guess, s);
+          launch_batch_state_init(items_d, nb, 1, s);
+          cudaEvent_t ev[2];
+          CK(cudaEventCreate(&ev[0]));
+          CK(cudaEventCreate(&ev[1]));
+          for (int c = 0; c < 3; ++c) {
+            if (c > 0)
+              CK(cudaMemcpyAsync(order_d, cand[c]->data(), sizeof(int) * (size_t)ntc,
+                                 cudaMemcpyHostToDevice, s));
+            const int* oc = c > 0 ? order_d : nullptr;
+            bool bad = false;
+            for (int rep = 0; rep < 3 && !bad; ++rep) {
+              if (rep == 1) CK(cudaEventRecord(ev[0], s));
+              bad = tc_launch_batch_gemm(1, items_d, nb, tinst_tc, oc, ntc, part, bf16,
+                                         kSplitScale, h->tcs, s) != 0;
+            }
+            CK(cudaEventRecord(ev[1], s));
+            CK(cudaEventSynchronize(ev[1]));
+            float t = 0.f;
+            if (bad || cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess) {
+              cudaEventDestroy(ev[0]);
+              cudaEventDestroy(ev[1]);
+              return fail(h, GCP_ERR_CUDA, "batched GEMM1 launch failed (work-order timing)");
+            }
+            ms[c] = t / 2.0;
+            if (ms[c] < ms[choice]) choice = c;
+          }
+          cudaEventDestroy(ev[0]);
+          cudaEventDestroy(ev[1]);
+        }
+        h->tune_key = tk;
+        h->tune_choice = choice;
+        for (int c = 0; c < 3; ++c) h->tune_ms[c] = ms[c];
+      }
+      if (h->tune_choice > 0)
+        CK(cudaMemcpyAsync(order_d, cand[h->tune_choice]->data(), sizeof(int) * (size_t)ntc,
+                           cudaMemcpyHostToDevice, s));
+    }
+    if (h->tune_choice > 0) order = order_d;
+  }
+
   Ctl c1{}, c0{};
   c1.stop = c0.stop = o.stop;
   c1.max_iter = c0.max_iter = o.max_iter;
@@ -1077,10 +1172,12 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   c1.method = c0.method = o.method;
 
   auto split_body = [&](cudaGraphConditionalHandle cond, cudaStream_t ss, int use_cond) {
-    if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, h->tcs, ss))
+    if (tc_launch_batch_gemm(1, items_d, nb, tinst_tc, order, ntc, part, bf16, kSplitScale,
+                             h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched GEMM1 launch failed");
     launch_batch_control(part, items_d, nb, c1, ss);
-    if (tc_launch_batch_gemm(2, items_d, nb, tinst_tc, ntc, part, bf16, kSplitScale, h->tcs, ss))
+    if (tc_launch_batch_gemm(2, items_d, nb, tinst_tc, order, ntc, part, bf16, kSplitScale,
+                             h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched GEMM2 launch failed");
     launch_batch_any_active(items_d, nb, (unsigned long long)cond, use_cond, active, ss);
     CK(cudaPeekAtLastError());
@@ -1101,13 +1198,13 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       return fail(h, GCP_ERR_CUDA, "batched slice GEMM launch failed");
     launch_batch_oz_finalize(items_d, nb, maxM, part, ss);
     launch_batch_control(part, items_d, nb, c0, ss);
-    if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, h->tcs, ss))
+    if (tc_launch_batch_gemm(3, items_d, nb, tinst_tc, order, ntc, part, 0, 1.0f, h->tcs, ss))
       return fail(h, GCP_ERR_CUDA, "batched refinement product launch failed");
     if (c0.stop == GCP_STOP_IDEMP_FRO) {
       // stop test of each new iterate from the split product of K = 3M
       // (as a single solve), instead of a further slice product
       launch_batch_check_halves(items_d, nb, maxM, ss);
-      if (tc_launch_batch_gemm(4, items_d, nb, tinst_tc, ntc, part, 0, 1.0f, h->tcs, ss))
+      if (tc_launch_batch_gemm(4, items_d, nb, tinst_tc, order, ntc, part, 0, 1.0f, h->tcs, ss))
         return fail(h, GCP_ERR_CUDA, "batched stop-test product launch failed");
       launch_batch_check_control(part, items_d, nb, c0, ss);
     }
@@ -1269,6 +1366,24 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
                                   h->D64[1], h->S64, h->part, h->gpart, h->st, h->hist, s, err,
                                   sizeof err);
   if (rc != GCP_OK) return fail(h, (gcp_status)rc, "%s", err);
+  return GCP_OK;
+}
+
+gcp_status gcp_set_batched_order(void* hv, int order) {
+  Handle* h = (Handle*)hv;
+  if (!h) return GCP_ERR_INVALID_ARG;
+  if (order < -1 || order > 2)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_set_batched_order: order must be -1, 0, 1 or 2");
+  h->tune_force = order;
+  return GCP_OK;
+}
+
+gcp_status gcp_batched_order(void* hv, int* choice, double* ms) {
+  Handle* h = (Handle*)hv;
+  if (!h || !choice) return GCP_ERR_INVALID_ARG;
+  *choice = h->tune_choice;
+  if (ms)
+    for (int c = 0; c < 3; ++c) ms[c] = h->tune_ms[c];
   return GCP_OK;
 }
 

@@ -341,8 +341,15 @@ void launch_batch_f64_gemm2(const BatchItem* items, int batch, const int* tile_i
 // Tensor-core products over the work list of all instances.
 int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* err, int errlen);
 size_t tc_map_bytes();
+// `order`: the order in which the CTAs take the work list's tiles (null: the
+// list's own); results do not depend on it.
 int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
-                         int ntiles, double* part, int bf16, float split_scale, float* scratch,
-                         cudaStream_t s);
+                         const int* order, int ntiles, double* part, int bf16, float split_scale,
+                         float* scratch, cudaStream_t s);
+// Estimated cost of tile `local` of an Mp x Mp instance's work list, in
+// units of one 32 x 32 block's epilogue: 2 for a block above the diagonal
+// (direct and mirrored stores), 1 for a diagonal block, plus Mp / 128 for the
+// products.
+int tc_tile_cost(int Mp, int local);
 
 }  // namespace gcp

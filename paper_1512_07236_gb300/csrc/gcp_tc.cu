@@ -65,11 +65,14 @@
 //     of a tile they store it to one of two scratch slots of this CTA in
 //     global memory (128 KB each, L2-resident) and start on the next tile;
 //   * warpgroup 3, four epilogue warps: the tile's epilogue from the scratch
-//     slot, rows 32 e.. for warp 12 + e, while the next tile accumulates;
-//     each warp mirrors its blocks through a 16 x 32 shared-memory buffer.
+//     slot while the next tile accumulates, its 32 x 32 blocks dealt
+//     round-robin to the four warps; each warp mirrors its blocks through a
+//     16 x 32 shared-memory buffer and prefetches into L2 the rows of the
+//     next tile that it will read from HBM.
 // So the MMA warp never waits for an epilogue (it waited ~25 % of a tile at
 // M = 8192 when the drain warps also ran the epilogue).  Register budgets
-// (setmaxnreg): 40 / 176 / 120 a thread against 128 at launch.  Blocks
+// (setmaxnreg): 40 / 176 / 120 a thread against 128 at launch (40 / 168 /
+// 136 in the batched kernels).  Blocks
 // below the diagonal are skipped; every element above the diagonal is
 // stored twice (direct and mirrored).  Every wait is bounded (2 s unless the
 // launch asks for less); on expiry the kernel records State::timeout and
@@ -108,8 +111,21 @@ constexpr int kThreads = 512;
 constexpr int kEpiWarp0 = 12;  // first epilogue warp
 constexpr int kEpiThreads = 128;
 constexpr int kEpiBarrier = 2;  // named barrier of the epilogue warps
-constexpr uint32_t kCtlRegs = 40, kDrainRegs = 176, kEpiRegs = 120;  // per thread
-static_assert(128 * kCtlRegs + 256 * kDrainRegs + 128 * kEpiRegs <= 65536, "register split");
+// Register split (setmaxnreg, per thread) against 128 a thread at launch:
+// the batched kernels, whose short-K tiles leave the drain warps idle and
+// the epilogue warps busy, move 8 registers a drain thread to the epilogue
+// (136, so a 32 x 32 block's loads are all in flight at once without
+// spilling).
+constexpr uint32_t kCtlRegs = 40;
+template <bool BATCHED>
+__host__ __device__ constexpr uint32_t drain_regs() { return BATCHED ? 168 : 176; }
+template <bool BATCHED>
+__host__ __device__ constexpr uint32_t epi_regs() { return BATCHED ? 136 : 120; }
+template <bool BATCHED>
+__host__ __device__ constexpr uint32_t split_regs() {
+  return 128 * kCtlRegs + 256 * drain_regs<BATCHED>() + 128 * epi_regs<BATCHED>();
+}
+static_assert(split_regs<false>() <= 65536 && split_regs<true>() <= 65536, "register split");
 constexpr uint32_t kABytes = BM * BK * 2;           // 8 KB
 constexpr uint32_t kBBytes = BN * BK * 2;           // 16 KB
 constexpr uint32_t kPartBytes = kABytes + kBBytes;  // 24 KB: the hi (or lo) part of a stage
@@ -147,6 +163,10 @@ struct Epi {
   const CUtensorMap* emaps;
   // drain -> epilogue hand-over: 2 slots of BM x BN floats per CTA
   float* scratch;
+  // batched: the order in which the CTAs take the tiles (position -> tile
+  // id of the work list), or null for the work list's own order; a tile's
+  // partials stay at its id
+  const int* order;
   unsigned long long wait_ns;  // bound of every wait
   int stall;  // diagnostic: the drain first waits on a barrier nobody arrives on
 };
@@ -158,7 +178,7 @@ struct Epi {
 // CTAs working at the same time then share a few A panels (rows) and the
 // super-column's B panels, which stay in L2 while the CTAs stream along K.
 constexpr int kGroupJ = 8;
-__device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
+__host__ __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
   for (int j0 = 0; j0 < NJ; j0 += kGroupJ) {
     const int j1 = j0 + kGroupJ < NJ ? j0 + kGroupJ : NJ;
     for (int i = 0; i < NI; ++i) {
@@ -329,16 +349,18 @@ __device__ __forceinline__ void gemm1_pass(const Epi& ep, const float* __restric
   const float is2 = ep.inv_s2;
   const int rs = lane >> 3, cl = 4 * (lane & 7);
   const size_t cbase = (size_t)ocol0 + cl;
+  // the whole block's loads in flight before its first store
+  float4 xv[8], yv[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int rr = rs + 4 * j;
+    xv[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(orow0 + rr) * Mp + cbase);
+    yv[j] = __ldcg(reinterpret_cast<const float4*>(yb + rr * ys + cl));
+  }
 #pragma unroll
   for (int jh = 0; jh < 8; jh += 4) {
-    // the block's loads in flight before its first store
-    float4 xx[4], yy[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int rr = rs + 4 * (jh + j);
-      xx[j] = *reinterpret_cast<const float4*>(ep.X + (size_t)(orow0 + rr) * Mp + cbase);
-      yy[j] = __ldcg(reinterpret_cast<const float4*>(yb + rr * ys + cl));
-    }
+    const float4* xx = xv + jh;
+    const float4* yy = yv + jh;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = orow0 + rs + 4 * (jh + j);
@@ -419,12 +441,12 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
   const float is2 = ep.inv_s2;
   const int rs = lane >> 3, cl = 4 * (lane & 7);
   const size_t cbase = (size_t)ocol0 + cl;
-  // two rows in flight per lane (three float4 operands each)
+  // four rows in flight per lane (three float4 operands each)
 #pragma unroll
-  for (int jh = 0; jh < 8; jh += 2) {
-    float4 xx[2], ss[2], yy[2];
+  for (int jh = 0; jh < 8; jh += 4) {
+    float4 xx[4], ss[4], yy[4];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < 4; ++j) {
       const int rr = rs + 4 * (jh + j);
       const size_t off = (size_t)(orow0 + rr) * Mp + cbase;
       xx[j] = *reinterpret_cast<const float4*>(ep.X + off);
@@ -434,7 +456,7 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
       }
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < 4; ++j) {
       const int r = orow0 + rs + 4 * (jh + j);
       const size_t off = (size_t)r * Mp + cbase;
       float4 o = xx[j];
@@ -464,14 +486,12 @@ __device__ __forceinline__ void gemm2_pass(const Epi& ep, const float* __restric
         }
       }
     }
-    if ((jh & 3) == 2) {
-      // rows 4 jh - 8 .. 4 jh + 7 of the block, mirrored
-      __syncwarp();
-      mirror_half(stage, Mp, orow0, ocol0, 4 * jh - 8, diag_blk,
-                  [&](size_t off, float4 o) { store_out4<BF16>(ep, off, o); },
-                  [&](size_t off, float v) { store_out1<BF16>(ep, off, v); });
-      __syncwarp();
-    }
+    // rows 4 jh .. 4 jh + 15 of the block, mirrored
+    __syncwarp();
+    mirror_half(stage, Mp, orow0, ocol0, 4 * jh, diag_blk,
+                [&](size_t off, float4 o) { store_out4<BF16>(ep, off, o); },
+                [&](size_t off, float v) { store_out1<BF16>(ep, off, v); });
+    __syncwarp();
   }
 }
 
@@ -528,6 +548,7 @@ __device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restric
 // Everything one tile needs: its block coordinates, operand maps, the
 // epilogue pointers of its instance and the update coefficients.
 struct TileCtx {
+  int g;  // tile id (index of its partials)
   int I, J, nkb;
   bool skip;  // instance stopped: no work at all
   bool mma;   // products needed (false: identity copy of the iterate)
@@ -542,6 +563,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
                                          const CUtensorMap* mBl, const BatchItem* items,
                                          const int* tile_inst, TileCtx& c) {
   c.ep = base;
+  c.g = t;
   if (!BATCHED) {
     if (MODE == 5)
       tc_tile_full(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
@@ -553,6 +575,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
     c.bh = mBh;
     c.bl = mBl;
   } else {
+    if (base.order) c.g = t = base.order[t];
     const BatchItem& it = items[tile_inst[t]];
     State* st = it.st;
     c.skip = st->stopped != 0;
@@ -812,7 +835,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&fin_bar, 0, wlim)) atomicOr(timeout_flag, 1);
     }
   } else if (warp < kEpiWarp0) {
-    reg_alloc<kDrainRegs>();
+    reg_alloc<drain_regs<BATCHED>()>();
     // ---------------- drain (warps 4..11) ----------------
     // TMEM lane quarter is fixed by the warp's rank within its warpgroup
     const int dw = warp - 4, q = warp & 3, half = dw >> 2;
@@ -878,15 +901,37 @@ __global__ void __launch_bounds__(kThreads, 1)
       ++u;
     }
   } else {
-    reg_dealloc<kEpiRegs>();
+    if constexpr (epi_regs<BATCHED>() > 128)
+      reg_alloc<epi_regs<BATCHED>()>();
+    else
+      reg_dealloc<epi_regs<BATCHED>()>();
     // ---------------- epilogue (warps 12..15) ----------------
-    const int e = warp - kEpiWarp0;  // rows 32 e .. 32 e + 31 of every tile
+    const int e = warp - kEpiWarp0;  // every fourth block of a tile; prefetches rows 32 e..
     const float* slots = ep.scratch + (size_t)blockIdx.x * 2 * kSlotFloats;
     uint32_t u = 0, nred = 0;
+    // L2 prefetch of the FP32 rows this warp reads from HBM in GEMM1 and
+    // GEMM2 (X, and Sigma when GEMM2 has products): row 32 e + lane of a
+    // tile, from the first 128-column block on or above the diagonal to the
+    // tile's last column, one bulk prefetch per operand.  Issued for the
+    // next tile halfway through the current one, so that the epilogue's
+    // loads hit L2 instead of waiting on HBM.
+    auto prefetch_rows = [&](const TileCtx& q) {
+      if constexpr (MODE == 1 || MODE == 2) {
+        if (q.skip) return;
+        const int h0 = 2 * q.J >= q.I ? 0 : 1;
+        const size_t off =
+            (size_t)(q.I * BM + 32 * e + lane) * q.ep.Mp + (size_t)q.J * BN + 128 * h0;
+        const uint32_t bytes = (uint32_t)(2 - h0) * 128 * sizeof(float);
+        l2_prefetch(q.ep.X + off, bytes);
+        if (MODE == 2 && q.mma) l2_prefetch(q.ep.Sig + off, bytes);
+      }
+    };
+    int pf_t = -1;  // the tile whose rows were prefetched ahead
     for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
       TileCtx c;
       make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
       if (c.skip) continue;  // uniform over the CTA
+      if (t != pf_t) prefetch_rows(c);
       const bool has = c.nkb > 0;
       const uint32_t slot = u & 1;
       bool ok = !(*(volatile int*)timeout_flag);
@@ -897,28 +942,49 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float* tile = slots + slot * kSlotFloats;
       double dpart[2] = {0.0, 0.0};  // diagonal sums (FP64)
       float pp[3] = {0.f, 0.f, 0.f};  // element sums (FP32 per lane)
-      const int row0 = c.I * BM + 32 * e;
       // does the tile reach the diagonal? (uniform: decides the FP64 sums)
       const bool tile_diag = (2 * c.J == c.I) || (2 * c.J + 1 == c.I);
       if (ok) {
+        float thf = 0.f, f2th = 0.f, thtb = 0.f;
+        if constexpr (MODE == 1) {
+          const double th = c.ep.st->theta;
+          thf = (float)th;
+          f2th = (float)(2.0 * th);
+          thtb = (float)(th * (1.0 - th));
+        }
+        // The tile's 32 x 32 blocks that the product writes (stripe s =
+        // rows 32 s.., column block p), taken in stripe order and dealt
+        // round-robin to the four epilogue warps: on a tile that reaches the
+        // diagonal the stripes hold different numbers of blocks, and one
+        // warp per stripe would leave the others waiting at the tile's
+        // barrier.
+        int q = 0;
 #pragma unroll 1
-        for (int p = 0; p < 8; ++p) {
+        for (int k = 0; k < 32; ++k) {
+          if ((MODE == 1 || MODE == 2) && k == 16 && t + (int)gridDim.x < ep.ntiles) {
+            TileCtx cn;
+            make_ctx<MODE, BATCHED>(t + gridDim.x, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst,
+                                    cn);
+            prefetch_rows(cn);
+            pf_t = t + gridDim.x;
+          }
+          const int sp = k >> 3, p = k & 7;
           const int half = p >> 2, part = p & 3;
           const int jb = 2 * c.J + half;  // 128-column block
           // below the diagonal: the mirror of another tile (all tiles are
           // computed in mode 5, a non-symmetric product)
           if (MODE != 5 && jb < c.I) continue;
-          if (MODE != 5 && jb == c.I && part < e) continue;
-          const bool dblk = MODE != 5 && jb == c.I && part == e;
+          if (MODE != 5 && jb == c.I && part < sp) continue;
+          if ((q++ & 3) != e) continue;
+          const bool dblk = MODE != 5 && jb == c.I && part == sp;
+          const int row0 = c.I * BM + 32 * sp;
           const int cl0 = half * 128 + part * 32;  // tile-local column of the block
           const int c0 = c.J * BN + cl0;
           // rows row0.., columns c0.. of the row-major scratch tile (and
           // their mirror, through this warp's staging buffer)
-          const float* yd = tile + (size_t)(32 * e) * BN + cl0;
+          const float* yd = tile + (size_t)(32 * sp) * BN + cl0;
           float* stage = epi_stage + e * kStageFloats;
           if constexpr (MODE == 1) {
-            const double th = c.ep.st->theta;
-            const float thf = (float)th, f2th = (float)(2.0 * th), thtb = (float)(th * (1.0 - th));
             gemm1_pass<BF16>(c.ep, yd, BN, row0, c0, dblk, thf, f2th, thtb, pp, dpart, stage);
           } else if constexpr (MODE == 2) {
             gemm2_pass<BF16>(c.ep, yd, BN, row0, c0, dblk, c.mma, c.ca, c.cb, c.cj, c.cz, stage);
@@ -968,7 +1034,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         double sacc = 0.0;
         if (lane < 5)
           for (int w = 0; w < 4; ++w) sacc += r[w * 5 + lane];
-        ep.part[(size_t)t * kPartFields + lane] = sacc;
+        ep.part[(size_t)c.g * kPartFields + lane] = sacc;
       }
       ++nred;
       if (stop) break;
@@ -1054,7 +1120,7 @@ int launch_tc(const TcOperands* A, const TcOperands* B, Epi ep, const BatchItem*
     // the drain warpgroups' setmaxnreg.inc would wait forever
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<MODE, BF16, BATCHED>) != cudaSuccess ||
-        fa.numRegs * kThreads < (int)(128 * kCtlRegs + 256 * kDrainRegs + 128 * kEpiRegs))
+        fa.numRegs * kThreads < (int)split_regs<BATCHED>())
       return 1;
     attr = true;
   }
@@ -1236,12 +1302,26 @@ int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* er
   return 0;
 }
 
+int tc_tile_cost(int Mp, int local) {
+  int I, J;
+  tc_tile(local, Mp / BM, Mp / BN, I, J);
+  int c = Mp / 128;
+  for (int sp = 0; sp < 4; ++sp)
+    for (int p = 0; p < 8; ++p) {
+      const int jb = 2 * J + (p >> 2), part = p & 3;
+      if (jb < I || (jb == I && part < sp)) continue;
+      c += (jb == I && part == sp) ? 1 : 2;
+    }
+  return c;
+}
+
 int tc_launch_batch_gemm(int mode, const BatchItem* items, int batch, const int* tile_inst,
-                         int ntiles, double* part, int bf16, float split_scale, float* scratch,
-                         cudaStream_t s) {
+                         const int* order, int ntiles, double* part, int bf16, float split_scale,
+                         float* scratch, cudaStream_t s) {
   (void)batch;
   Epi ep{};
   ep.scratch = scratch;
+  ep.order = order;
   ep.part = part;
   ep.ntiles = ntiles;
   ep.split_scale = split_scale;

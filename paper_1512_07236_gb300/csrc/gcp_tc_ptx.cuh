@@ -62,6 +62,12 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// Asynchronous L2 prefetch of `bytes` bytes at global address `p` (both
+// multiples of 16, the range inside one allocation): a hint, nothing waits.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((uint64_t)p), "r"(bytes)
+               : "memory");
+}
 // Shared-memory matrix descriptor: K-major, SWIZZLE_64B (64-byte rows,
 // 8-row groups 512 B apart = SBO), descriptor version 1 (bits 46-47).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {

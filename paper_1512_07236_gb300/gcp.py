@@ -30,7 +30,7 @@ HISTORY_FIELDS = 8
 EXPORTS = ("gcp_default_options", "gcp_status_string", "gcp_create", "gcp_destroy",
            "gcp_last_error", "gcp_init_guess", "gcp_step", "gcp_solve", "gcp_get_history",
            "gcp_solve_batched", "gcp_backward", "gcp_time_kernels", "gcp_solve_noalloc",
-           "gcp_debug_timeout")
+           "gcp_debug_timeout", "gcp_set_batched_order", "gcp_batched_order")
 
 
 class Options(C.Structure):
@@ -94,9 +94,12 @@ def load_library(path: str = LIB_PATH):
         lib.gcp_solve_noalloc.argtypes = [vp, ip, ip, ip, ip, vp, ip, ip, C.POINTER(Result),
                                           C.POINTER(Options), C.c_char_p, ip]
         lib.gcp_debug_timeout.argtypes = [vp, ip, dp, C.POINTER(Options)]
+        lib.gcp_set_batched_order.argtypes = [vp, ip]
+        lib.gcp_batched_order.argtypes = [vp, C.POINTER(ip), C.POINTER(dp)]
         for name in ("gcp_create", "gcp_destroy", "gcp_init_guess", "gcp_step", "gcp_solve",
                      "gcp_get_history", "gcp_solve_batched", "gcp_backward", "gcp_time_kernels",
-                     "gcp_solve_noalloc", "gcp_debug_timeout"):
+                     "gcp_solve_noalloc", "gcp_debug_timeout", "gcp_set_batched_order",
+                     "gcp_batched_order"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -297,6 +300,19 @@ class Solver:
         if p in (PRECISIONS["mixed_fp16"], PRECISIONS["mixed_bf16"]):
             return ms[0], ms[1], ms[2], int(ms[3])
         return ms[0], ms[1]
+
+    def set_batched_order(self, order=-1):
+        """gcp_set_batched_order: -1 times the candidate work orders of the
+        batched tensor-core products; 0, 1 or 2 fixes one."""
+        self._check(self.lib.gcp_set_batched_order(self.h, int(order)))
+
+    def batched_order(self):
+        """gcp_batched_order: (order used by the last split-precision batched
+        solve, [GEMM1 ms of each candidate, -1 where not timed])."""
+        c = C.c_int()
+        ms = (C.c_double * 3)()
+        self._check(self.lib.gcp_batched_order(self.h, C.byref(c), ms))
+        return c.value, list(ms)
 
     def debug_timeout(self, M, wait_s=1e-3):
         """gcp_debug_timeout: run one split GEMM1 of size M whose waits are

@@ -142,3 +142,45 @@ def test_batched_host_loop_matches_graph(solver, batch):
     for a, b, x, y in zip(D1, D2, i1, i2):
         assert x["iters"] == y["iters"]
         assert torch.equal(a, b)
+
+
+def _tc_tiles(M):
+    """Tensor-core tiles of one instance: 128 x 256 tiles of the padded
+    matrix that reach the upper block triangle."""
+    Mp = -(-M // 256) * 256
+    NI, NJ = Mp // 128, Mp // 256
+    return sum(min(2 * j + 2, NI) for j in range(NJ))
+
+
+def test_batched_work_orders_agree(solver):
+    """The batched tensor-core products take their tiles in one of three
+    orders (scheduling only): every order gives the same D bit for bit, a
+    fixed order is reported back untimed, and the timed choice on a batch of
+    at least two tiles per SM measures every candidate and keeps the
+    fastest."""
+    items = inputs.batched_rotated(96, sizes=tuple(range(64, 1025, 96)), seed=11,
+                                   qr_backend="torch")
+    Hs = [_dev(H) for H, _, _, _ in items]
+    Ns = [N for _, N, _, _ in items]
+    kw = dict(prec="mixed_fp16", tol=1e-8)
+    try:
+        ref = None
+        for order in (0, 1, 2):
+            solver.set_batched_order(order)
+            Ds, infos = solver.solve_batched(Hs, Ns, **kw)
+            c, ms = solver.batched_order()
+            assert c == order and ms == [-1.0, -1.0, -1.0]
+            assert all(i["status"] == 0 for i in infos)
+            if ref is None:
+                ref = Ds
+            else:
+                assert all(torch.equal(a, b) for a, b in zip(Ds, ref))
+        solver.set_batched_order(-1)
+        Ds, infos = solver.solve_batched(Hs, Ns, **kw)
+        c, ms = solver.batched_order()
+        assert all(torch.equal(a, b) for a, b in zip(Ds, ref))
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        assert sum(_tc_tiles(H.shape[0]) for H in Hs) >= 2 * nsm
+        assert all(m > 0 for m in ms) and ms[c] == min(ms)
+    finally:
+        solver.set_batched_order(-1)
