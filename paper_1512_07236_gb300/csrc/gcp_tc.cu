@@ -67,8 +67,8 @@
 //   * warpgroup 3, four epilogue warps: the tile's epilogue from the scratch
 //     slot while the next tile accumulates, its 32 x 32 blocks dealt
 //     round-robin to the four warps; each warp mirrors its blocks through a
-//     16 x 32 shared-memory buffer and prefetches into L2 the rows of the
-//     next tile that it will read from HBM.
+//     16 x 32 shared-memory buffer and, in batched launches, prefetches into
+//     L2 the rows of the next tile that it will read from HBM.
 // So the MMA warp never waits for an epilogue (it waited ~25 % of a tile at
 // M = 8192 when the drain warps also ran the epilogue).  Register budgets
 // (setmaxnreg): 40 / 176 / 120 a thread against 128 at launch (40 / 168 /
@@ -909,12 +909,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int e = warp - kEpiWarp0;  // every fourth block of a tile; prefetches rows 32 e..
     const float* slots = ep.scratch + (size_t)blockIdx.x * 2 * kSlotFloats;
     uint32_t u = 0, nred = 0;
-    // L2 prefetch of the FP32 rows this warp reads from HBM in GEMM1 and
-    // GEMM2 (X, and Sigma when GEMM2 has products): row 32 e + lane of a
-    // tile, from the first 128-column block on or above the diagonal to the
-    // tile's last column, one bulk prefetch per operand.  Issued for the
-    // next tile halfway through the current one, so that the epilogue's
-    // loads hit L2 instead of waiting on HBM.
+    // Batched (short-K) tiles, whose epilogue bounds the launch: L2
+    // prefetch of the FP32 rows this warp reads from HBM in GEMM1 and GEMM2
+    // (X, and Sigma when GEMM2 has products): row 32 e + lane of a tile,
+    // from the first 128-column block on or above the diagonal to the
+    // tile's last column, one bulk prefetch per operand, issued for the
+    // next tile halfway through the current one.
     auto prefetch_rows = [&](const TileCtx& q) {
       if constexpr (MODE == 1 || MODE == 2) {
         if (q.skip) return;
@@ -931,7 +931,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       TileCtx c;
       make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
       if (c.skip) continue;  // uniform over the CTA
-      if (t != pf_t) prefetch_rows(c);
+      if (BATCHED && t != pf_t) prefetch_rows(c);
       const bool has = c.nkb > 0;
       const uint32_t slot = u & 1;
       bool ok = !(*(volatile int*)timeout_flag);
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int q = 0;
 #pragma unroll 1
         for (int k = 0; k < 32; ++k) {
-          if ((MODE == 1 || MODE == 2) && k == 16 && t + (int)gridDim.x < ep.ntiles) {
+          if ((MODE == 1 || MODE == 2) && BATCHED && k == 16 && t + (int)gridDim.x < ep.ntiles) {
             TileCtx cn;
             make_ctx<MODE, BATCHED>(t + gridDim.x, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst,
                                     cn);
