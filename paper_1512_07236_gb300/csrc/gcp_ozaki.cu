@@ -390,6 +390,24 @@ __device__ __forceinline__ void oz_ctx(int t, const CUtensorMap* maps, const dou
 // instance.  Batched: the work list `tile_inst` (the tensor-core tile list of
 // the batch) names each tile's instance; every instance's operands come from
 // its BatchItem, and tiles of stopped instances are skipped.
+// The CTA's (pass, tile) work items in order.  Single products run pass-major
+// (every tile of pass p before pass p + 1: the CTAs stream the same two
+// digit slices at a time).  Batched products, whose tiles have K <= 1024 and
+// whose drains' FP64 read-modify-write per pass outweighs the products, run
+// tile-major: a tile's passes one after the other, so that its FP64 output
+// stays in L2 between them.  Each element sums the passes in the same order
+// either way.
+template <bool BATCHED>
+__device__ __forceinline__ void oz_work(int it, int npass, int ntl, int& ps, int& t) {
+  if (BATCHED) {
+    t = blockIdx.x + (it / npass) * gridDim.x;
+    ps = it % npass;
+  } else {
+    ps = it / ntl;
+    t = blockIdx.x + (it % ntl) * gridDim.x;
+  }
+}
+
 template <bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ OzMaps maps, const __grid_constant__ OzPlan plan,
@@ -429,13 +447,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
+  // this CTA's tiles, and its (pass, tile) work items
+  const int ntl = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nwork = plan.npass * ntl;
 
   if (warp == 0) {
     if (lane == 0) {
       uint32_t g = 0;
       bool alive = true;
-      for (int ps = 0; ps < plan.npass && alive; ++ps)
-        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      for (int it = 0; it < nwork && alive; ++it) {
+        {
+          int ps, t;
+          oz_work<BATCHED>(it, plan.npass, ntl, ps, t);
           OzTile c;
           oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
           if (c.skip) continue;
@@ -458,6 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                           c.J * BN + 128);
             }
         }
+      }
       const uint32_t first = g > STAGES ? g - STAGES : 0;
       for (uint32_t k = first; k < g; ++k)
         if (!mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1)) atomicOr(tflag, 1);
@@ -467,8 +491,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_f16(0);
       uint32_t g = 0, qc = 0;
       bool alive = true;
-      for (int ps = 0; ps < plan.npass && alive; ++ps) {
-        for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      for (int it = 0; it < nwork && alive; ++it) {
+        {
+          int ps, t;
+          oz_work<BATCHED>(it, plan.npass, ntl, ps, t);
           OzTile c;
           oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
           if (c.skip) continue;
@@ -515,10 +541,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 dw * 32 * 32;
     uint32_t qc = 0;
     bool alive = true;
-    for (int ps = 0; ps < plan.npass && alive; ++ps) {
+    for (int it = 0; it < nwork && alive; ++it) {
+      int ps, t;
+      oz_work<BATCHED>(it, plan.npass, ntl, ps, t);
       const double wscale = ldexp(1.0, -plan.db * (plan.w[ps] + 2));  // B^-(w+2)
       const bool first_pass = ps == 0, last_pass = ps == plan.npass - 1;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      {
         OzTile c;
         oz_ctx<BATCHED>(t, maps.m, rscale, S, M, Mp, items, tile_inst, c);
         if (c.skip) continue;
