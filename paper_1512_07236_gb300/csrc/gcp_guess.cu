@@ -442,7 +442,7 @@ void launch_batch_guess(const BatchItem* items, int batch, int maxM, int h_f64, 
     return (int)(b < 1 ? 1 : (b > 64 ? 64 : b));
   };
   if (split) {
-    const int maxMp = ((maxM + 255) / 256) * 256;
+    const int maxMp = tc_pad(maxM);
     dim3 g(ew((long long)maxMp * maxMp), batch);
     if (bf16) {
       if (h_f64)

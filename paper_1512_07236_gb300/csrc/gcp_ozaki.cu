@@ -373,7 +373,7 @@ __device__ __forceinline__ void oz_ctx(int t, const CUtensorMap* maps, const dou
     c.rscale = rscale;
     c.S = S;
     c.skip = false;
-    oz_tile(t, Mp / BM, Mp / BN, c.I, c.J);
+    oz_tile(t, Mp / BM, (Mp + BN - 1) / BN, c.I, c.J);
   } else {
     const BatchItem& it = items[tile_inst[t]];
     c.skip = it.st->stopped != 0;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void oz_ctx(int t, const CUtensorMap* maps, const dou
     c.maps = (const CUtensorMap*)it.oz_maps;
     c.rscale = it.oz_rs;
     c.S = it.S64;
-    oz_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
+    oz_tile(t - it.tc_off, it.Mp / BM, (it.Mp + BN - 1) / BN, c.I, c.J);
   }
 }
 

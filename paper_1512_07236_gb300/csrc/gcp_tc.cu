@@ -178,6 +178,10 @@ struct Epi {
 // CTAs working at the same time then share a few A panels (rows) and the
 // super-column's B panels, which stay in L2 while the CTAs stream along K.
 constexpr int kGroupJ = 8;
+// Column blocks of 256 over an Mp x Mp operand (Mp a multiple of 128): the
+// last one reaches past the matrix by 128 columns when Mp / 128 is odd; its
+// B rows there load as zeros (TMA fill) and its blocks there are not stored.
+__host__ __device__ __forceinline__ int nj_blocks(int Mp) { return (Mp + BN - 1) / BN; }
 __host__ __device__ __forceinline__ void tc_tile(int t, int NI, int NJ, int& I, int& J) {
   for (int j0 = 0; j0 < NJ; j0 += kGroupJ) {
     const int j1 = j0 + kGroupJ < NJ ? j0 + kGroupJ : NJ;
@@ -566,9 +570,9 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
   c.g = t;
   if (!BATCHED) {
     if (MODE == 5)
-      tc_tile_full(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
+      tc_tile_full(t, base.Mp / BM, nj_blocks(base.Mp), c.I, c.J);
     else
-      tc_tile(t, base.Mp / BM, base.Mp / BN, c.I, c.J);
+      tc_tile(t, base.Mp / BM, nj_blocks(base.Mp), c.I, c.J);
     c.skip = false;
     c.ah = mAh;
     c.al = mAl;
@@ -632,7 +636,7 @@ __device__ __forceinline__ void make_ctx(int t, const Epi& base, const CUtensorM
       c.ep.rs_d = it.oz_rs;
       c.ep.ld64 = it.M;
     }
-    tc_tile(t - it.tc_off, it.Mp / BM, it.Mp / BN, c.I, c.J);
+    tc_tile(t - it.tc_off, it.Mp / BM, nj_blocks(it.Mp), c.I, c.J);
   }
   const State* st = c.ep.st;
   c.mma = !c.skip && (MODE == 1 || MODE >= 5 || st->apply != 0);
@@ -919,9 +923,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (MODE == 1 || MODE == 2) {
         if (q.skip) return;
         const int h0 = 2 * q.J >= q.I ? 0 : 1;
-        const size_t off =
-            (size_t)(q.I * BM + 32 * e + lane) * q.ep.Mp + (size_t)q.J * BN + 128 * h0;
-        const uint32_t bytes = (uint32_t)(2 - h0) * 128 * sizeof(float);
+        const int cs = q.J * BN + 128 * h0, ce = q.J * BN + BN < q.ep.Mp ? q.J * BN + BN : q.ep.Mp;
+        if (ce <= cs) return;
+        const size_t off = (size_t)(q.I * BM + 32 * e + lane) * q.ep.Mp + cs;
+        const uint32_t bytes = (uint32_t)(ce - cs) * sizeof(float);
         l2_prefetch(q.ep.X + off, bytes);
         if (MODE == 2 && q.mma) l2_prefetch(q.ep.Sig + off, bytes);
       }
@@ -975,6 +980,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // computed in mode 5, a non-symmetric product)
           if (MODE != 5 && jb < c.I) continue;
           if (MODE != 5 && jb == c.I && part < sp) continue;
+          if (128 * jb >= c.ep.Mp) continue;  // past the matrix (last column block)
           if ((q++ & 3) != e) continue;
           const bool dblk = MODE != 5 && jb == c.I && part == sp;
           const int row0 = c.I * BM + 32 * sp;
@@ -1073,7 +1079,7 @@ int encode_map(CUtensorMap* m, const void* ptr, int Mp, int bf16, char* err, int
                int box_k = BK) {
   EncodeTiledFn enc = get_encode(err, errlen);
   if (!enc) return 1;
-  if (((uintptr_t)ptr & 15u) != 0 || ((size_t)Mp * 2) % 16 != 0 || Mp % BN != 0) {
+  if (((uintptr_t)ptr & 15u) != 0 || ((size_t)Mp * 2) % 16 != 0 || Mp % BM != 0) {
     snprintf(err, errlen, "tensor map: misaligned operand or size");
     return 1;
   }
@@ -1141,7 +1147,7 @@ int launch_tc(const TcOperands* A, const TcOperands* B, Epi ep, const BatchItem*
 }
 }  // namespace
 
-int tc_pad(int M) { return ((M + BN - 1) / BN) * BN; }
+int tc_pad(int M) { return ((M + BM - 1) / BM) * BM; }
 
 size_t tc_scratch_bytes() { return (size_t)sm_count() * 2 * kSlotFloats * sizeof(float); }
 
@@ -1150,7 +1156,7 @@ int tc_encode_map(void* map, const void* ptr, int Mp, int bf16, char* err, int e
 }
 
 int tc_num_tiles(int Mp) {
-  const int NI = Mp / BM, NJ = Mp / BN;
+  const int NI = Mp / BM, NJ = nj_blocks(Mp);
   int n = 0;
   for (int j = 0; j < NJ; ++j) n += (2 * j + 2 < NI ? 2 * j + 2 : NI);
   return n;
@@ -1287,7 +1293,7 @@ int tc_launch_product(const TcOperands* A, const TcOperands* B, float* C, int Mp
     ep.ntiles = tc_num_tiles(Mp);
     return launch_tc<6, false, false>(A, B, ep, nullptr, nullptr, s);
   }
-  ep.ntiles = (Mp / BM) * (Mp / BN);
+  ep.ntiles = (Mp / BM) * nj_blocks(Mp);
   return launch_tc<5, false, false>(A, B, ep, nullptr, nullptr, s);
 }
 
@@ -1304,12 +1310,12 @@ int tc_build_batch_maps(void* maps_host, const BatchItem& it, int bf16, char* er
 
 int tc_tile_cost(int Mp, int local) {
   int I, J;
-  tc_tile(local, Mp / BM, Mp / BN, I, J);
+  tc_tile(local, Mp / BM, nj_blocks(Mp), I, J);
   int c = Mp / 128;
   for (int sp = 0; sp < 4; ++sp)
     for (int p = 0; p < 8; ++p) {
       const int jb = 2 * J + (p >> 2), part = p & 3;
-      if (jb < I || (jb == I && part < sp)) continue;
+      if (jb < I || (jb == I && part < sp) || 128 * jb >= Mp) continue;
       c += (jb == I && part == sp) ? 1 : 2;
     }
   return c;
