@@ -229,6 +229,9 @@ __device__ __forceinline__ void tc_tile_full(int t, int NI, int NJ, int& I, int&
 // the relative accuracy of the split product because |X| is small.  The
 // general step of Eq. hpcp3 is the same plus (1 - 2c)(D - S); the control
 // kernel sets c within 1/2 +- 0.05 to put Tr D+ back at N.
+// Columns whose FP64 operands a refinement or stop-test thread loads at once.
+constexpr int kSegGroup = 4;
+
 __device__ __forceinline__ void refine_seg(const Epi& ep, int row, int c_base, bool diag_blk,
                                            const float* __restrict__ src) {
   if (row >= ep.M) return;
@@ -236,15 +239,28 @@ __device__ __forceinline__ void refine_seg(const Epi& ep, int row, int c_base, b
   load_row32(src, acc);
   const double wr = 1.0 / (kRefScale * ep.rs_x[row]);  // powers of two: exact
   const double g = ep.st->a;
+  // a group of columns' loads in flight before their stores
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    const int c = c_base + k;
-    if (c >= ep.M || (diag_blk && c < row)) continue;
-    const size_t o = (size_t)row * ep.ld64 + c;
-    const double sv = ep.S64[o];
-    const double v = sv - 2.0 * (wr * ep.rs_d[c]) * (double)acc[k] - g * (sv - ep.D64[o]);
-    ep.Dn64[o] = v;
-    if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
+  for (int k0 = 0; k0 < 32; k0 += kSegGroup) {
+    double sv[kSegGroup], dv[kSegGroup], rd[kSegGroup];
+#pragma unroll
+    for (int j = 0; j < kSegGroup; ++j) {
+      const int c = c_base + k0 + j;
+      const bool ok = c < ep.M && !(diag_blk && c < row);
+      const size_t o = (size_t)row * ep.ld64 + c;
+      sv[j] = ok ? ep.S64[o] : 0.0;
+      dv[j] = ok ? ep.D64[o] : 0.0;
+      rd[j] = ok ? ep.rs_d[c] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kSegGroup; ++j) {
+      const int c = c_base + k0 + j;
+      if (c >= ep.M || (diag_blk && c < row)) continue;
+      const size_t o = (size_t)row * ep.ld64 + c;
+      const double v = sv[j] - 2.0 * (wr * rd[j]) * (double)acc[k0 + j] - g * (sv[j] - dv[j]);
+      ep.Dn64[o] = v;
+      if (c != row) ep.Dn64[(size_t)c * ep.ld64 + row] = v;
+    }
   }
 }
 
@@ -260,18 +276,31 @@ __device__ __forceinline__ void check_seg(const Epi& ep, int row, int c_base, bo
   if (row >= ep.M) return;
   float acc[32];
   load_row32(src, acc);
+  // a group of columns' loads in flight at a time
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    const int c = c_base + k;
-    if (c >= ep.M || (diag_blk && c < row)) continue;
-    const size_t o = (size_t)row * ep.ld64 + c;
-    const double sw = ep.S64[o] + (double)(acc[k] * inv_scale);  // D1^2, exact scaling
-    const double d1 = ep.D64[o];
-    const float x1 = (float)(sw - d1);
-    pp[1] = fmaf((c == row ? 1.f : 2.f) * x1, x1, pp[1]);
-    if (c == row) {
-      dpart[0] += d1;
-      dpart[1] += sw;
+  for (int k0 = 0; k0 < 32; k0 += kSegGroup) {
+    double sv[kSegGroup], dv[kSegGroup];
+#pragma unroll
+    for (int j = 0; j < kSegGroup; ++j) {
+      const int c = c_base + k0 + j;
+      const bool ok = c < ep.M && !(diag_blk && c < row);
+      const size_t o = (size_t)row * ep.ld64 + c;
+      sv[j] = ok ? ep.S64[o] : 0.0;
+      dv[j] = ok ? ep.D64[o] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kSegGroup; ++j) {
+      const int k = k0 + j;
+      const int c = c_base + k;
+      if (c >= ep.M || (diag_blk && c < row)) continue;
+      const double sw = sv[j] + (double)(acc[k] * inv_scale);  // D1^2, exact scaling
+      const double d1 = dv[j];
+      const float x1 = (float)(sw - d1);
+      pp[1] = fmaf((c == row ? 1.f : 2.f) * x1, x1, pp[1]);
+      if (c == row) {
+        dpart[0] += d1;
+        dpart[1] += sw;
+      }
     }
   }
 }
