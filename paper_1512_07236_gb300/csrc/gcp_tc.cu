@@ -538,12 +538,14 @@ __device__ __forceinline__ void plain_pass(const Epi& ep, const float* __restric
   const int lane = threadIdx.x & 31;
   const int rs = lane >> 3, cl = 4 * (lane & 7);
   const float sc = ep.inv_s2;
+  // the whole block's loads in flight before its first store
+  float4 yv[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    yv[j] = __ldcg(reinterpret_cast<const float4*>(yb + (rs + 4 * j) * ys + cl));
 #pragma unroll
   for (int jh = 0; jh < 8; jh += 4) {
-    float4 yy[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      yy[j] = __ldcg(reinterpret_cast<const float4*>(yb + (rs + 4 * (jh + j)) * ys + cl));
+    const float4* yy = yv + jh;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = orow0 + rs + 4 * (jh + j);
