@@ -151,7 +151,9 @@ def test_autograd_function(solver):
                                           (1000, 250, 40, 16, 0.05)])
 def test_fp32_adjoint_matches_fp64_adjoint(solver, M, N, K, ck, gap):
     """The FP32 adjoint (products on the tensor cores, padded to a multiple
-    of 256: M = 300, 513 and 1000 leave ragged tiles) against the FP64 one on
+    of 128: M = 300 and 513 pad to 384 and 640, where the last 256-wide
+    column block reaches past the matrix; 1000 leaves ragged tiles) against
+    the FP64 one on
     the same FP32-rounded inputs.  K either stops before the McWeeny endgame
     of the FP32 recursion or runs well past convergence, where both
     recursions have the same limit."""

@@ -35,8 +35,9 @@ def _dev(a, dtype=torch.float64):
 @pytest.mark.parametrize("prec,tol", [("fp16x3", 2e-6), ("bf16x3", 6e-5)])
 @pytest.mark.parametrize("M", [256, 300, 640])
 def test_single_split_step(solver, prec, tol, M):
-    """One tensor-core step from a mid-purification D (several 128x256 tiles,
-    ragged tail when M is not a multiple of 256)."""
+    """One tensor-core step from a mid-purification D (several 128x256 tiles;
+    M = 300 pads to 384, so the last 256-wide column block reaches past the
+    matrix; 640 pads to itself with an odd number of 128-row blocks)."""
     N = M // 4
     H, _, _ = inputs.rotated_spectrum(M, N, seed=M)
     D, _ = o.canonical_guess(H, N)
