@@ -544,7 +544,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int it = 0; it < nwork && alive; ++it) {
       int ps, t;
       oz_work<BATCHED>(it, plan.npass, ntl, ps, t);
-      const double wscale = ldexp(1.0, -plan.db * (plan.w[ps] + 2));  // B^-(w+2)
+      // B^-(w+2), applied in FP32: the pass sums are integers below 2^24, so
+      // the product is exact (B^-(w+2) >= 2^-60 stays normal)
+      const float wscale = ldexpf(1.0f, -plan.db * (plan.w[ps] + 2));
       const bool first_pass = ps == 0, last_pass = ps == plan.npass - 1;
       {
         OzTile c;
@@ -583,7 +585,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int k = 0; k < 32; ++k) a[k] = tp[k * 32 + (lane ^ k)];
           __syncwarp();
           const int cc = c_base + part * 32 + lane;
-          const double cs = cc < Mi ? c.rscale[cc] * wscale : 0.0;
+          // the row and column scales 2^(e_i + e_j) multiply the tile once,
+          // on its last pass: the passes add unscaled terms, and power-of-
+          // two scaling commutes with the rounding of the FP64 additions
+          // (the result equals scaling every term, short of underflow)
+          const double cs = (last_pass && cc < Mi) ? c.rscale[cc] : 0.0;
           double old[32];
           if (!first_pass) {
 #pragma unroll
@@ -596,11 +602,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const int rk = row0 + k;
-            const double rsk = __shfl_sync(0xffffffffu, rs_row, k);
             const bool ok = rk < Mi && cc < Mi && !(diag && cc < rk);
-            // every factor is a power of two or an integer below 2^24: exact
-            const double v = (double)a[k] * cs * rsk;
-            if (ok) Si[(size_t)rk * Mi + cc] = first_pass ? v : old[k] + v;
+            const double v = (double)(a[k] * wscale);  // exact
+            double x = first_pass ? v : old[k] + v;
+            if (last_pass) x *= cs * __shfl_sync(0xffffffffu, rs_row, k);
+            if (ok) Si[(size_t)rk * Mi + cc] = x;
           }
         }
         tc_fence_before();
