@@ -19,7 +19,9 @@
 //     P (B/2)^2 M <= 2^24, so every partial sum is an integer below 2^24 and
 //     the FP32 tensor-core accumulation is exact whatever its rounding mode
 //     (b = 6 at M = 8192: P = 2; b = 5: P = 8);
-//   * each pass's integer sums are scaled and added in FP64.
+//   * each pass's integer sums are weighted by B^-(w+2) (in FP32, exactly)
+//     and added in FP64; the row and column scales multiply the sum once,
+//     after the tile's last pass.
 //
 // Kernel layout: persistent CTAs over the 128 x 256 tiles of the upper block
 // triangle, pass-major (every CTA runs pass p over its tiles before pass
