@@ -63,7 +63,8 @@
 //     32 (w % 4).. and columns 128 ((w - 4) / 4).. of each chunk and keeps
 //     the tile's 128 x 256 FP32 sum in registers (128 a thread); at the end
 //     of a tile they store it to one of two scratch slots of this CTA in
-//     global memory (128 KB each, L2-resident) and start on the next tile;
+//     global memory (128 KB each, L2-resident) and start on the next tile
+//     (a non-symmetric plain product, mode 5, they store scaled themselves);
 //   * warpgroup 3, four epilogue warps: the tile's epilogue from the scratch
 //     slot while the next tile accumulates, its 32 x 32 blocks dealt
 //     round-robin to the four warps; each warp mirrors its blocks through a
@@ -917,6 +918,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&acce_bar[b]);
       }
       if (!alive) break;
+      if constexpr (MODE == 5) {
+        // a non-symmetric plain product's epilogue is a scaled copy: the
+        // drain stores its row's 128 columns itself (the same products as
+        // the epilogue's, C = inv_s2 (A B)), skipping the scratch round trip
+        const int col0 = c.J * BN + half * 128;
+        if (col0 < c.ep.Mp) {
+          const float sc = c.ep.inv_s2;
+          float4* dst = reinterpret_cast<float4*>(
+              c.ep.out + (size_t)(c.I * BM + 32 * q + lane) * c.ep.Mp + col0);
+#pragma unroll
+          for (int k = 0; k < 32; ++k)
+            dst[k] = make_float4(acc[4 * k] * sc, acc[4 * k + 1] * sc, acc[4 * k + 2] * sc,
+                                 acc[4 * k + 3] * sc);
+        }
+        continue;
+      }
       // hand the tile to the epilogue warps through scratch slot u & 1
       const uint32_t slot = u & 1;
       if (u >= 2 && !__all_sync(0xffffffffu, mbar_wait(&sempty_bar[slot], ((u >> 1) - 1) & 1, wlim))) {
@@ -941,6 +958,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     else
       reg_dealloc<epi_regs<BATCHED>()>();
     // ---------------- epilogue (warps 12..15) ----------------
+    // (none in mode 5: the drain warps store the product)
     const int e = warp - kEpiWarp0;  // every fourth block of a tile; prefetches rows 32 e..
     const float* slots = ep.scratch + (size_t)blockIdx.x * 2 * kSlotFloats;
     uint32_t u = 0, nred = 0;
@@ -963,7 +981,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     int pf_t = -1;  // the tile whose rows were prefetched ahead
-    for (int t = blockIdx.x; t < ep.ntiles; t += gridDim.x) {
+    for (int t = blockIdx.x; MODE != 5 && t < ep.ntiles; t += gridDim.x) {
       TileCtx c;
       make_ctx<MODE, BATCHED>(t, ep, &mAh, &mAl, &mBh, &mBl, items, tile_inst, c);
       if (c.skip) continue;  // uniform over the CTA
