@@ -335,9 +335,11 @@ def run_workload(args, rank):
             "speedup_vs_loop": loop_ms / ms if loop_ms else None,
             "effective_tflops": flops / (ms * 1e-3) / 1e12,
             "by_size": buckets,
-            "work_order": {"choice": ["instance-major", "cost-sorted", "cost-sorted snake"][order_choice],
+            "work_order": {"choice": ["instance-major", "cost-sorted", "cost-sorted snake",
+                                      "instance-major, largest first"][order_choice],
                            "gemm1_ms": {"instance-major": order_ms[0], "cost-sorted": order_ms[1],
-                                        "cost-sorted snake": order_ms[2]}},
+                                        "cost-sorted snake": order_ms[2],
+                                        "instance-major, largest first": order_ms[3]}},
             "status_ok": sum(1 for i in infos if i["status"] == 0),
             "max_subspace_err_first32": max(errs), "clocks": clk.summary()})
     elif args.workload == "pbar":

@@ -249,18 +249,19 @@ gcp_status gcp_solve_batched(void* handle, int batch, const void* const* H, cons
  * counterpart in the paper).  In split-precision batched solves the CTAs
  * take the tiles of all instances' products from one work list; the first
  * solve for a given set of instance sizes (with at least two tiles per SM)
- * times the first step's GEMM1 under three candidate orders and keeps the
+ * times the first step's GEMM1 under four candidate orders and keeps the
  * fastest for later solves of those sizes on this handle: 0 = instance after
  * instance, 1 = tiles by estimated cost, largest first, dealt to the CTAs in
- * turn, 2 = as 1 with every other round dealt in reverse.  Results are the
- * same under every order, bit for bit.
+ * turn, 2 = as 1 with every other round dealt in reverse, 3 = instance after
+ * instance, largest instance first.  Results are the same under every
+ * order, bit for bit.
  *
- * gcp_set_batched_order: order = -1 (default) times the candidates; 0, 1
- * or 2 fixes that candidate without timing.  GCP_ERR_INVALID_ARG otherwise.
- * gcp_batched_order: *choice = the order the last split-precision batched
- * solve used; ms (3 doubles, may be NULL) = the GEMM1 time of each
- * candidate in milliseconds, -1 where none was timed (fewer tiles, or a
- * fixed order).  Host-only; no device work. */
+ * gcp_set_batched_order: order = -1 (default) times the candidates; 0, 1,
+ * 2 or 3 fixes that candidate without timing.  GCP_ERR_INVALID_ARG
+ * otherwise.  gcp_batched_order: *choice = the order the last
+ * split-precision batched solve used; ms (4 doubles, may be NULL) = the
+ * GEMM1 time of each candidate in milliseconds, -1 where none was timed
+ * (fewer tiles, or a fixed order).  Host-only; no device work. */
 gcp_status gcp_set_batched_order(void* handle, int order);
 gcp_status gcp_batched_order(void* handle, int* choice, double* ms);
 

@@ -74,7 +74,7 @@ struct Handle {
   std::vector<int> tune_key;
   int tune_force = -1;  // gcp_set_batched_order: a fixed candidate, or -1
   int tune_choice = 0;
-  double tune_ms[3] = {-1.0, -1.0, -1.0};
+  double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};
   // adjoint workspaces (checkpoints, segment iterates, adjoint buffers):
   // FP64 and FP32 (tensor-core) forms
   void* adj = nullptr;
@@ -1072,7 +1072,9 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   // with each candidate: (0) the work list's own order, instance after
   // instance; (1) the tiles by estimated cost (tc_tile_cost), largest first,
   // dealt to the CTAs in turn; (2) the same, each round of one tile per CTA
-  // dealt in the reverse direction of the one before.  A tile's arithmetic
+  // dealt in the reverse direction of the one before; (3) instance after
+  // instance as in (0), the instances by size, largest first (an instance's
+  // tiles stay together, and share their operand panels in L2).  A tile's arithmetic
   // and its partials' place do not depend on the CTA that runs it, so the
   // results are the same under every order.
   const int* order = nullptr;
@@ -1088,7 +1090,8 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const int G = ntc < nsm ? ntc : nsm;  // CTAs of a launch
-      std::vector<int> cost(ntc), lpt(ntc), snake(ntc);
+      std::vector<int> cost(ntc), lpt(ntc), snake(ntc), bysize;
+      bysize.reserve(ntc);
       for (int k = 0; k < nb; ++k)
         for (int t = 0; t < items[k].tc_n; ++t)
           cost[items[k].tc_off + t] = tc_tile_cost(items[k].Mp, t);
@@ -1100,10 +1103,18 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
         const int width = ntc - r0 < G ? ntc - r0 : G;
         snake[t] = (round & 1) ? lpt[r0 + width - 1 - pos] : lpt[t];
       }
-      const std::vector<int>* cand[3] = {nullptr, &lpt, &snake};
+      {
+        std::vector<int> inst(nb);
+        for (int k = 0; k < nb; ++k) inst[k] = k;
+        std::stable_sort(inst.begin(), inst.end(),
+                         [&items](int a, int b) { return items[a].Mp > items[b].Mp; });
+        for (int k : inst)
+          for (int t = 0; t < items[k].tc_n; ++t) bysize.push_back(items[k].tc_off + t);
+      }
+      const std::vector<int>* cand[4] = {nullptr, &lpt, &snake, &bysize};
       if (retune) {
         int choice = 0;
-        double ms[3] = {-1.0, -1.0, -1.0};
+        double ms[4] = {-1.0, -1.0, -1.0, -1.0};
         if (h->tune_force >= 0) {
           choice = h->tune_force;
         } else if (ntc >= 2 * G) {
@@ -1115,7 +1126,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
           cudaEvent_t ev[2];
           CK(cudaEventCreate(&ev[0]));
           CK(cudaEventCreate(&ev[1]));
-          for (int c = 0; c < 3; ++c) {
+          for (int c = 0; c < 4; ++c) {
             if (c > 0)
               CK(cudaMemcpyAsync(order_d, cand[c]->data(), sizeof(int) * (size_t)ntc,
                                  cudaMemcpyHostToDevice, s));
@@ -1142,7 +1153,7 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
         }
         h->tune_key = tk;
         h->tune_choice = choice;
-        for (int c = 0; c < 3; ++c) h->tune_ms[c] = ms[c];
+        for (int c = 0; c < 4; ++c) h->tune_ms[c] = ms[c];
       }
       if (h->tune_choice > 0)
         CK(cudaMemcpyAsync(order_d, cand[h->tune_choice]->data(), sizeof(int) * (size_t)ntc,
@@ -1372,8 +1383,8 @@ gcp_status gcp_backward(void* hv, const void* H, int M, int N, int ld, int h_dty
 gcp_status gcp_set_batched_order(void* hv, int order) {
   Handle* h = (Handle*)hv;
   if (!h) return GCP_ERR_INVALID_ARG;
-  if (order < -1 || order > 2)
-    return fail(h, GCP_ERR_INVALID_ARG, "gcp_set_batched_order: order must be -1, 0, 1 or 2");
+  if (order < -1 || order > 3)
+    return fail(h, GCP_ERR_INVALID_ARG, "gcp_set_batched_order: order must be -1, 0, 1, 2 or 3");
   h->tune_force = order;
   return GCP_OK;
 }
@@ -1383,7 +1394,7 @@ gcp_status gcp_batched_order(void* hv, int* choice, double* ms) {
   if (!h || !choice) return GCP_ERR_INVALID_ARG;
   *choice = h->tune_choice;
   if (ms)
-    for (int c = 0; c < 3; ++c) ms[c] = h->tune_ms[c];
+    for (int c = 0; c < 4; ++c) ms[c] = h->tune_ms[c];
   return GCP_OK;
 }
 

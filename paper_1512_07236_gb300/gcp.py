@@ -303,14 +303,14 @@ class Solver:
 
     def set_batched_order(self, order=-1):
         """gcp_set_batched_order: -1 times the candidate work orders of the
-        batched tensor-core products; 0, 1 or 2 fixes one."""
+        batched tensor-core products; 0, 1, 2 or 3 fixes one."""
         self._check(self.lib.gcp_set_batched_order(self.h, int(order)))
 
     def batched_order(self):
         """gcp_batched_order: (order used by the last split-precision batched
         solve, [GEMM1 ms of each candidate, -1 where not timed])."""
         c = C.c_int()
-        ms = (C.c_double * 3)()
+        ms = (C.c_double * 4)()
         self._check(self.lib.gcp_batched_order(self.h, C.byref(c), ms))
         return c.value, list(ms)
 

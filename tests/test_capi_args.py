@@ -142,16 +142,16 @@ def test_debug_timeout_rejects(lib, handle, M, wait_s):
 
 
 def test_batched_order_args(lib, handle):
-    """gcp_set_batched_order takes -1, 0, 1 or 2; gcp_batched_order reports the
+    """gcp_set_batched_order takes -1, 0, 1, 2 or 3; gcp_batched_order reports the
     default (order 0, nothing timed) on a fresh handle; both are host-only."""
-    for bad in (-2, 3, 100):
+    for bad in (-2, 4, 100):
         assert lib.gcp_set_batched_order(handle, bad) == gcp.ERR_INVALID_ARG
     assert lib.gcp_set_batched_order(None, 0) == gcp.ERR_INVALID_ARG
-    for good in (-1, 0, 1, 2, -1):
+    for good in (-1, 0, 1, 2, 3, -1):
         assert lib.gcp_set_batched_order(handle, good) == gcp.OK
     c = C.c_int(-7)
-    ms = (C.c_double * 3)(1.0, 1.0, 1.0)
+    ms = (C.c_double * 4)(1.0, 1.0, 1.0, 1.0)
     assert lib.gcp_batched_order(handle, C.byref(c), ms) == gcp.OK
-    assert c.value == 0 and list(ms) == [-1.0, -1.0, -1.0]
+    assert c.value == 0 and list(ms) == [-1.0, -1.0, -1.0, -1.0]
     assert lib.gcp_batched_order(handle, None, ms) == gcp.ERR_INVALID_ARG
     assert lib.gcp_batched_order(None, C.byref(c), ms) == gcp.ERR_INVALID_ARG

@@ -153,7 +153,7 @@ def _tc_tiles(M):
 
 
 def test_batched_work_orders_agree(solver):
-    """The batched tensor-core products take their tiles in one of three
+    """The batched tensor-core products take their tiles in one of four
     orders (scheduling only): every order gives the same D bit for bit, a
     fixed order is reported back untimed, and the timed choice on a batch of
     at least two tiles per SM measures every candidate and keeps the
@@ -165,11 +165,11 @@ def test_batched_work_orders_agree(solver):
     kw = dict(prec="mixed_fp16", tol=1e-8)
     try:
         ref = None
-        for order in (0, 1, 2):
+        for order in (0, 1, 2, 3):
             solver.set_batched_order(order)
             Ds, infos = solver.solve_batched(Hs, Ns, **kw)
             c, ms = solver.batched_order()
-            assert c == order and ms == [-1.0, -1.0, -1.0]
+            assert c == order and ms == [-1.0, -1.0, -1.0, -1.0]
             assert all(i["status"] == 0 for i in infos)
             if ref is None:
                 ref = Ds
