@@ -1074,9 +1074,9 @@ gcp_status gcp_solve_batched(void* hv, int batch, const void* const* H, const in
   // dealt to the CTAs in turn; (2) the same, each round of one tile per CTA
   // dealt in the reverse direction of the one before; (3) instance after
   // instance as in (0), the instances by size, largest first (an instance's
-  // tiles stay together, and share their operand panels in L2).  A tile's arithmetic
-  // and its partials' place do not depend on the CTA that runs it, so the
-  // results are the same under every order.
+  // tiles stay together, and share their operand panels in L2).  A tile's
+  // arithmetic and its partials' place do not depend on the CTA that runs
+  // it, so the results are the same under every order.
   const int* order = nullptr;
   if (split && ntc > 0) {
     std::vector<int> tk;
